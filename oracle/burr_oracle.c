@@ -1,0 +1,548 @@
+/*
+ * burr_oracle.c -- serial CPU oracle for Bumped Ribbon Retrieval (BuRR)
+ * construction with bumping at partition ("thread") boundaries.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the ground truth that the CUDA
+ * library is checked against.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA path.
+ *
+ * It follows the method step by step, in the paper's order:
+ *   - the retrieval problem f: S -> {0,1}^r                   (Sec. 1, abstract)
+ *   - one GF(2) equation per key whose coefficients lie in a window of width
+ *     w that starts at the key's hashed start slot ("spatial coupling")  (Sec. 2, Fig. 1)
+ *   - sort the equations by start slot                       (Sec. 4, sort via IPS2Ra)
+ *   - on-the-fly Gaussian elimination bucket by bucket, bumping a prefix of a
+ *     bucket on failure, the prefix given by a 2-bit threshold (four levels,
+ *     one bumping nothing and one bumping the whole bucket)     (Sec. 2, "Bumping")
+ *   - overloading: more equations than slots per layer          (Sec. 2, last para.)
+ *   - parallel construction: the equation system is cut into partitions and the
+ *     first bucket after every cut bumps at least w-1 slots, so no kept equation
+ *     overlaps a cut and partitions are independent             (Sec. 3, "Bumping")
+ *   - back-substitution                                         (Sec. 4, Fig. 7)
+ *   - bumped keys go to the next layer; 4 layers, then a base case that cannot
+ *     bump and is scaled up until it solves                     (Sec. 3, Sec. 4)
+ *   - the query: AND the key's coefficients with the table window and take the
+ *     parity, one bit per value bit                              (Sec. 2)
+ *
+ * Where the paper is silent (it defers to the SEA'22 BuRR paper) this oracle
+ * takes one written reading; each reading is marked "READING" below.
+ *
+ * Parity pins: every function here is pinned by tests that do not reuse this
+ * code (known-answer vectors of SplitMix64, an inverse of the mixer, a dense
+ * GF(2) brute-force solver, the query invariant, permutation invariance).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#include "burr_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Hashing (READING: the paper defers the hash to SEA'22).                   */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014), a bijection
+ * on 64-bit words. */
+uint64_t or_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+#define OR_GOLDEN 0x9E3779B97F4A7C15ULL
+
+/* Seed of hash layer `index` (bumping layers 0..L-1, base-case attempt a at
+ * index L+a). */
+uint64_t or_layer_seed(uint64_t seed, uint64_t index)
+{
+    return or_mix64(seed ^ ((index + 1) * OR_GOLDEN));
+}
+
+/* floor(a*b / 2^64): Lemire's multiply-shift range reduction. */
+static uint64_t or_mulhi(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+}
+
+/* The equation of one key in a layer with m slots: start slot s in
+ * [0, m-w] and a w-bit coefficient row whose bit k stands for slot s+k;
+ * bit 0 is always set. */
+void or_hash(uint64_t key, uint64_t sigma, uint64_t m, uint32_t w,
+             uint64_t *start, uint64_t *coeff)
+{
+    uint64_t h = or_mix64(key ^ sigma);
+    *start = or_mulhi(h, m - w + 1);
+    *coeff = or_mix64(h + sigma) | 1ULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sizing and partitioning (READING: overload factor and cut placement).     */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t or_align64(uint64_t x) { return (x + 63) & ~63ULL; }
+
+/* Slots of a bumping layer holding n keys at load alpha (keys per slot). */
+uint64_t or_layer_slots(uint64_t n, double alpha, uint32_t w)
+{
+    if (n == 0) return 0;
+    return or_align64((uint64_t)ceil((double)n / alpha) + w);
+}
+
+/* Slots of the base case for n keys, attempt a: the first size leaves
+ * `slack` spare rows, every retry grows it by 10%. */
+uint64_t or_fallback_slots(uint64_t n, double slack, uint32_t w, uint32_t attempt)
+{
+    if (n == 0) return 0;
+    uint64_t m = or_align64((uint64_t)ceil((double)n * (1.0 + slack)) + w);
+    for (uint32_t a = 0; a < attempt; a++)
+        m = or_align64((uint64_t)ceil((double)m * 1.1));
+    return m;
+}
+
+/* Number of 128-slot (B-slot) buckets of start positions: starts are 0..m-w. */
+uint64_t or_num_buckets(uint64_t m, uint32_t w, uint32_t B)
+{
+    if (m == 0) return 0;
+    return (m - w + B) / B;
+}
+
+/* Number of partitions of a layer with m slots (minimum-buckets-per-thread
+ * analogue, Sec. 3): layers below min_slots, or smaller than two partitions,
+ * are one partition; otherwise floor(m/P) partitions, the last one taking the
+ * remainder.  Cut j (j >= 1) sits at start slot j*P. */
+uint64_t or_num_partitions(uint64_t m, uint64_t P, uint64_t min_slots)
+{
+    if (m == 0) return 0;
+    if (m < min_slots || m < P) return 1;
+    return m / P;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One layer: sort, insert with bumping, back-substitute.                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t key;
+    uint32_t val;
+    uint64_t start;
+    uint64_t coeff;
+} or_row;
+
+/* Equations ordered by bucket ascending, then offset descending (inside a
+ * bucket the rows are inserted from the bucket's end towards its start, so
+ * that a threshold bumps a prefix).  Ties are broken by key only to make the
+ * oracle deterministic; the result does not depend on it. */
+static uint32_t g_B;
+static int or_row_cmp(const void *pa, const void *pb)
+{
+    const or_row *a = (const or_row *)pa, *b = (const or_row *)pb;
+    uint64_t ba = a->start / g_B, bb = b->start / g_B;
+    if (ba != bb) return ba < bb ? -1 : 1;
+    uint64_t oa = a->start % g_B, ob = b->start % g_B;
+    if (oa != ob) return oa > ob ? -1 : 1;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return 0;
+}
+
+/* On-the-fly Gaussian elimination of one equation into the band (C = stored
+ * coefficient rows, C[p] has bit 0 = pivot p, 0 = empty slot; Y = stored
+ * right-hand sides).  Returns the slot it was stored in, or -1 if the
+ * coefficients vanished (READING: a vanishing row is a failure whatever its
+ * right-hand side). */
+static int64_t or_insert(uint64_t *C, uint32_t *Y, uint64_t start, uint64_t coeff,
+                         uint32_t val, uint64_t *steps)
+{
+    uint64_t cur = coeff, p = start;
+    uint32_t y = val;
+    for (;;) {
+        if (cur == 0) return -1;
+        int tz = __builtin_ctzll(cur);
+        p += (uint64_t)tz;
+        cur >>= tz;
+        if (C[p] == 0) {
+            C[p] = cur;
+            Y[p] = y;
+            return (int64_t)p;
+        }
+        cur ^= C[p];
+        y ^= Y[p];
+        (*steps)++;
+    }
+}
+
+/* Smallest level strictly above offset o. */
+static uint32_t or_level_above(const uint32_t levels[4], uint32_t o)
+{
+    for (int i = 0; i < 4; i++)
+        if (levels[i] > o) return (uint32_t)i;
+    return 3;
+}
+
+/* Smallest level that bumps at least w-1 slots after a cut.  READING: we take
+ * the smallest level >= w, which for w=64 and levels {0,32,64,128} is the
+ * level 64 either way and places the ownership boundary between partitions at
+ * cut + w, a multiple of 64. */
+int or_forced_code(const uint32_t levels[4], uint32_t w)
+{
+    for (int i = 0; i < 4; i++)
+        if (levels[i] >= w) return i;
+    return -1;
+}
+
+/*
+ * Build one layer.  keys/vals: n input pairs (vals masked to r bits).
+ * m slots, hash seed sigma, cuts[0..ncuts) strictly increasing multiples of B
+ * (start slots where a new partition begins; empty = one partition).
+ * fallback != 0: base case -- no thresholds, every row must insert.
+ * Outputs: thresh[ceil(nb/32)] packed 2-bit codes (ignored for fallback),
+ * z[(m/64)*r] interleaved bit planes, bumped keys/vals (capacity n).
+ * Returns 0, OR_FAIL (fallback could not solve) or OR_EINVAL.
+ */
+int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                   uint32_t r, uint64_t m, uint64_t sigma,
+                   const uint32_t levels[4], uint32_t B, uint32_t w,
+                   const uint64_t *cuts, uint64_t ncuts, int fallback,
+                   uint64_t *thresh, uint64_t *z,
+                   uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                   or_stats *st)
+{
+    *nbumped = 0;
+    if (n == 0 || m == 0) return 0;
+    if (w != 64 || m % 64 != 0 || m < w) return OR_EINVAL;
+    uint32_t mask = (r >= 32) ? 0xFFFFFFFFu : ((1u << r) - 1u);
+    uint64_t nb = or_num_buckets(m, w, B);
+    int forced = or_forced_code(levels, w);
+    if (forced < 0 && ncuts > 0) return OR_EINVAL;
+
+    /* 1. hash every key to its equation */
+    or_row *rows = (or_row *)malloc(sizeof(or_row) * n);
+    if (!rows) return OR_ENOMEM;
+    for (uint64_t i = 0; i < n; i++) {
+        rows[i].key = keys[i];
+        rows[i].val = vals[i] & mask;
+        or_hash(keys[i], sigma, m, w, &rows[i].start, &rows[i].coeff);
+    }
+    /* 2. sort by start slot (bucket asc, offset desc) */
+    g_B = B;
+    qsort(rows, n, sizeof(or_row), or_row_cmp);
+
+    uint64_t *C = (uint64_t *)calloc(m, sizeof(uint64_t));
+    uint32_t *Y = (uint32_t *)calloc(m, sizeof(uint32_t));
+    int64_t *slot_of = (int64_t *)malloc(sizeof(int64_t) * n);
+    if (!C || !Y || !slot_of) { free(rows); free(C); free(Y); free(slot_of); return OR_ENOMEM; }
+    if (!fallback) {
+        /* every bucket that starts a partition j >= 1 carries the forced level,
+         * also when no key falls into it */
+        memset(thresh, 0, sizeof(uint64_t) * ((nb + 31) / 32));
+        for (uint64_t q = 0; q < ncuts; q++) {
+            uint64_t b = cuts[q] / B;
+            if (b < nb) thresh[b / 32] |= (uint64_t)forced << (2 * (b % 32));
+        }
+    }
+
+    /* 3. insertion, bucket by bucket */
+    uint64_t i = 0, cut_idx = 0;
+    int status = 0;
+    while (i < n) {
+        uint64_t b = rows[i].start / B;
+        uint64_t j = i;
+        while (j < n && rows[j].start / B == b) j++;
+        /* rows[i..j) is bucket b in descending offset order */
+        while (cut_idx < ncuts && cuts[cut_idx] < b * B) cut_idx++;
+        int after_cut = (cut_idx < ncuts && cuts[cut_idx] == b * B);
+        uint32_t t = (after_cut && !fallback) ? levels[forced] : 0;
+        uint32_t code = (after_cut && !fallback) ? (uint32_t)forced : 0;
+        for (uint64_t k = i; k < j; k++) slot_of[k] = -1;
+        for (uint64_t k = i; k < j; k++) {
+            uint32_t off = (uint32_t)(rows[k].start % B);
+            if (off < t) break;              /* forced bump below the level */
+            int64_t p = or_insert(C, Y, rows[k].start, rows[k].coeff, rows[k].val,
+                                  st ? &st->xor_steps : &(uint64_t){0});
+            if (st) st->inserted++;
+            if (p >= 0) {
+                slot_of[k] = p;
+                if (st && (uint64_t)p - rows[k].start > st->max_drift)
+                    st->max_drift = (uint64_t)p - rows[k].start;
+                continue;
+            }
+            if (fallback) { status = OR_FAIL; break; }
+            code = or_level_above(levels, off);
+            if (after_cut && code < (uint32_t)forced) code = (uint32_t)forced;
+            t = levels[code];
+            /* roll back every row of this bucket below the new threshold */
+            for (uint64_t q = i; q < k; q++) {
+                uint32_t oq = (uint32_t)(rows[q].start % B);
+                if (oq < t && slot_of[q] >= 0) {
+                    C[slot_of[q]] = 0;
+                    Y[slot_of[q]] = 0;
+                    slot_of[q] = -1;
+                }
+            }
+            break;
+        }
+        if (status) break;
+        if (!fallback) {
+            thresh[b / 32] &= ~(3ULL << (2 * (b % 32)));
+            thresh[b / 32] |= (uint64_t)code << (2 * (b % 32));
+            for (uint64_t k = i; k < j; k++) {
+                if ((uint32_t)(rows[k].start % B) < t) {
+                    bumped_keys[*nbumped] = rows[k].key;
+                    bumped_vals[*nbumped] = rows[k].val;
+                    (*nbumped)++;
+                }
+            }
+        }
+        i = j;
+    }
+
+    /* 4. back-substitution, right to left, free slots fixed to 0 (READING:
+     * the paper is silent on free variables).  Per-slot r-bit values first,
+     * then packed into bit planes. */
+    if (status == 0) {
+        uint32_t *Zs = (uint32_t *)calloc(m + 64, sizeof(uint32_t));
+        if (!Zs) status = OR_ENOMEM;
+        else {
+            for (uint64_t s = m; s-- > 0;) {
+                if (C[s] == 0) { Zs[s] = 0; continue; }
+                uint32_t v = Y[s];
+                for (int k = 1; k < 64; k++)
+                    if ((C[s] >> k) & 1ULL) v ^= Zs[s + (uint64_t)k];
+                Zs[s] = v;
+            }
+            memset(z, 0, sizeof(uint64_t) * (m / 64) * r);
+            for (uint64_t s = 0; s < m; s++)
+                for (uint32_t k = 0; k < r; k++)
+                    if ((Zs[s] >> k) & 1u)
+                        z[(s / 64) * r + k] |= 1ULL << (s % 64);
+            free(Zs);
+        }
+    }
+    free(rows); free(C); free(Y); free(slot_of);
+    return status;
+}
+
+/* Value stored for slot s, plane k, in the interleaved layout. */
+static uint32_t or_zbit(const uint64_t *z, uint32_t r, uint64_t s, uint32_t k)
+{
+    return (uint32_t)((z[(s / 64) * r + k] >> (s % 64)) & 1ULL);
+}
+
+/* Query one key against one layer's table: XOR of the r-bit slot values
+ * selected by the coefficient bits. */
+static uint32_t or_layer_eval(const uint64_t *z, uint32_t r, uint64_t s, uint64_t c)
+{
+    uint32_t v = 0;
+    for (int k = 0; k < 64; k++) {
+        if (!((c >> k) & 1ULL)) continue;
+        for (uint32_t q = 0; q < r; q++)
+            v ^= or_zbit(z, r, s + (uint64_t)k, q) << q;
+    }
+    return v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole structure.                                                          */
+/* ------------------------------------------------------------------------ */
+
+void or_default_params(or_params *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->r = 8;
+    p->w = 64;
+    p->B = 128;
+    p->levels[0] = 0; p->levels[1] = 32; p->levels[2] = 64; p->levels[3] = 128;
+    p->alpha = 1.015;   /* calibrated: ~1.0% total overhead at n=2^20, r=8 */
+    p->layers = 4;
+    p->partition_slots = 65536;
+    p->min_partition_slots = 65536;
+    p->seed = 0x5EED5EED5EED5EEDULL;
+    p->fb_max_retries = 16;
+    p->fb_slack = 0.1;
+}
+
+void or_free(or_struct *s)
+{
+    if (!s) return;
+    for (uint32_t l = 0; l <= OR_MAX_LAYERS; l++) {
+        free(s->layer[l].thresh);
+        free(s->layer[l].z);
+    }
+    memset(s, 0, sizeof(*s));
+}
+
+/*
+ * Build the whole layered structure.  cut_P[l] overrides the partition size
+ * of layer l (0 = use params); this lets tests give the oracle explicit cut
+ * lists.  Returns 0, OR_UNSOLVABLE, OR_EINVAL or OR_ENOMEM.
+ */
+int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+             const or_params *p, or_struct *out, or_stats *st)
+{
+    memset(out, 0, sizeof(*out));
+    if (p->r < 1 || p->r > 32 || p->w != 64 || p->B % 64 != 0 || p->B < 64 ||
+        p->layers > OR_MAX_LAYERS || p->levels[0] != 0 || p->levels[3] != p->B ||
+        !(p->levels[0] < p->levels[1] && p->levels[1] < p->levels[2] &&
+          p->levels[2] < p->levels[3]) ||
+        p->partition_slots % p->B != 0 || p->partition_slots == 0 ||
+        !(p->alpha > 0.0) || or_forced_code(p->levels, p->w) < 0)
+        return OR_EINVAL;
+    out->params = *p;
+    out->n = n;
+    uint32_t mask = (p->r >= 32) ? 0xFFFFFFFFu : ((1u << p->r) - 1u);
+
+    uint64_t *ck = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    uint32_t *cv = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint64_t *nk = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    uint32_t *nv = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    if (!ck || !cv || !nk || !nv) { free(ck); free(cv); free(nk); free(nv); return OR_ENOMEM; }
+    for (uint64_t i = 0; i < n; i++) { ck[i] = keys[i]; cv[i] = vals[i] & mask; }
+    uint64_t cn = n;
+    int status = 0;
+
+    for (uint32_t l = 0; l < p->layers && status == 0; l++) {
+        or_layer *L = &out->layer[l];
+        L->n = cn;
+        L->m = or_layer_slots(cn, p->alpha, p->w);
+        L->seed_index = l;
+        L->nbuckets = or_num_buckets(L->m, p->w, p->B);
+        uint64_t P = p->partition_slots;
+        if (p->cut_P[l]) P = p->cut_P[l];
+        L->nparts = or_num_partitions(L->m, P, p->min_partition_slots);
+        L->part_slots = P;
+        uint64_t ncuts = L->nparts ? L->nparts - 1 : 0;
+        uint64_t *cuts = (uint64_t *)malloc(sizeof(uint64_t) * (ncuts ? ncuts : 1));
+        for (uint64_t j = 0; j < ncuts; j++) cuts[j] = (j + 1) * P;
+        L->thresh = (uint64_t *)calloc((L->nbuckets + 31) / 32 + 1, sizeof(uint64_t));
+        L->z = (uint64_t *)calloc((L->m / 64) * p->r + 1, sizeof(uint64_t));
+        uint64_t nb = 0;
+        if (!cuts || !L->thresh || !L->z) status = OR_ENOMEM;
+        else
+            status = or_build_layer(ck, cv, cn, p->r, L->m,
+                                    or_layer_seed(p->seed, l), p->levels, p->B, p->w,
+                                    cuts, ncuts, 0, L->thresh, L->z, nk, nv, &nb, st);
+        free(cuts);
+        L->nbumped = nb;
+        if (st) st->bumped[l] = nb;
+        uint64_t *tk = ck; ck = nk; nk = tk;
+        uint32_t *tv = cv; cv = nv; nv = tv;
+        cn = nb;
+    }
+
+    /* base case: no bumping, grow until it solves */
+    if (status == 0) {
+        or_layer *F = &out->layer[OR_MAX_LAYERS];
+        F->n = cn;
+        status = OR_UNSOLVABLE;
+        for (uint32_t a = 0; a <= p->fb_max_retries; a++) {
+            free(F->z);
+            F->m = or_fallback_slots(cn, p->fb_slack, p->w, a);
+            F->seed_index = p->layers + a;
+            F->nbuckets = or_num_buckets(F->m, p->w, p->B);
+            F->nparts = F->m ? 1 : 0;
+            F->z = (uint64_t *)calloc((F->m / 64) * p->r + 1, sizeof(uint64_t));
+            if (!F->z) { status = OR_ENOMEM; break; }
+            uint64_t nb = 0;
+            int rc = or_build_layer(ck, cv, cn, p->r, F->m,
+                                    or_layer_seed(p->seed, F->seed_index), p->levels,
+                                    p->B, p->w, NULL, 0, 1, NULL, F->z, nk, nv, &nb, st);
+            if (rc == 0) { status = 0; out->fb_attempt = a; break; }
+            if (rc != OR_FAIL) { status = rc; break; }
+        }
+    }
+    free(ck); free(cv); free(nk); free(nv);
+    if (status) or_free(out);
+    return status;
+}
+
+/* Query: walk the layers; a key whose offset lies below its bucket's
+ * threshold was bumped and continues in the next layer. */
+uint32_t or_query_one(const or_struct *s, uint64_t key)
+{
+    const or_params *p = &s->params;
+    for (uint32_t l = 0; l < p->layers; l++) {
+        const or_layer *L = &s->layer[l];
+        if (L->m == 0) return 0;
+        uint64_t st, c;
+        or_hash(key, or_layer_seed(p->seed, L->seed_index), L->m, p->w, &st, &c);
+        uint64_t b = st / p->B;
+        uint32_t off = (uint32_t)(st % p->B);
+        uint32_t code = (uint32_t)((L->thresh[b / 32] >> (2 * (b % 32))) & 3ULL);
+        if (off < p->levels[code]) continue;
+        return or_layer_eval(L->z, p->r, st, c);
+    }
+    const or_layer *F = &s->layer[OR_MAX_LAYERS];
+    if (F->m == 0) return 0;
+    uint64_t st, c;
+    or_hash(key, or_layer_seed(p->seed, F->seed_index), F->m, p->w, &st, &c);
+    return or_layer_eval(F->z, p->r, st, c);
+}
+
+void or_query(const or_struct *s, const uint64_t *keys, uint32_t *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++) out[i] = or_query_one(s, keys[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Canonical export: little-endian u32/u64 fields, then the arrays.          */
+/* ------------------------------------------------------------------------ */
+
+static uint8_t *put32(uint8_t *q, uint32_t v) { memcpy(q, &v, 4); return q + 4; }
+static uint8_t *put64(uint8_t *q, uint64_t v) { memcpy(q, &v, 8); return q + 8; }
+
+uint64_t or_export(const or_struct *s, uint8_t *buf, uint64_t cap)
+{
+    const or_params *p = &s->params;
+    uint64_t need = 4 * 10 + 8 * 4 + (uint64_t)p->layers * 8 * 5 + 8 * 4;
+    for (uint32_t l = 0; l < p->layers; l++)
+        need += 8 * ((s->layer[l].nbuckets + 31) / 32) + 8 * (s->layer[l].m / 64) * p->r;
+    need += 8 * (s->layer[OR_MAX_LAYERS].m / 64) * p->r;
+    if (!buf || cap < need) return need;
+    uint8_t *q = buf;
+    q = put32(q, 0x52525542u); /* "BURR" */
+    q = put32(q, 1);
+    q = put32(q, p->r); q = put32(q, p->w); q = put32(q, p->B); q = put32(q, p->layers);
+    for (int i = 0; i < 4; i++) q = put32(q, p->levels[i]);
+    uint64_t abits; memcpy(&abits, &p->alpha, 8);
+    q = put64(q, p->seed); q = put64(q, abits); q = put64(q, s->n);
+    q = put64(q, 0);
+    for (uint32_t l = 0; l < p->layers; l++) {
+        const or_layer *L = &s->layer[l];
+        q = put64(q, L->n); q = put64(q, L->m); q = put64(q, L->nparts);
+        q = put64(q, L->nbuckets); q = put64(q, L->nbumped);
+    }
+    const or_layer *F = &s->layer[OR_MAX_LAYERS];
+    q = put64(q, F->n); q = put64(q, F->m); q = put64(q, F->seed_index);
+    q = put64(q, s->fb_attempt);
+    for (uint32_t l = 0; l < p->layers; l++) {
+        const or_layer *L = &s->layer[l];
+        uint64_t nw = (L->nbuckets + 31) / 32;
+        memcpy(q, L->thresh, 8 * nw); q += 8 * nw;
+        uint64_t nz = (L->m / 64) * p->r;
+        memcpy(q, L->z, 8 * nz); q += 8 * nz;
+    }
+    uint64_t nz = (F->m / 64) * p->r;
+    memcpy(q, F->z, 8 * nz); q += 8 * nz;
+    return (uint64_t)(q - buf);
+}
+
+/* Space accounting: bits of all tables and thresholds, over r*n. */
+double or_overhead(const or_struct *s)
+{
+    const or_params *p = &s->params;
+    if (s->n == 0) return 0.0;
+    double bits = 0;
+    for (uint32_t l = 0; l < p->layers; l++)
+        bits += (double)s->layer[l].m * p->r + 2.0 * (double)s->layer[l].nbuckets;
+    bits += (double)s->layer[OR_MAX_LAYERS].m * p->r;
+    return bits / ((double)p->r * (double)s->n) - 1.0;
+}
+
+/* Accessors for the ctypes wrapper. */
+const or_layer *or_get_layer(const or_struct *s, uint32_t l) { return &s->layer[l]; }
+uint64_t or_struct_size(void) { return sizeof(or_struct); }
+uint64_t or_stats_size(void) { return sizeof(or_stats); }
+uint64_t or_params_size(void) { return sizeof(or_params); }
+uint64_t or_layer_size(void) { return sizeof(or_layer); }

@@ -1,0 +1,75 @@
+/*
+ * burr_oracle.h -- serial CPU oracle of BuRR construction (test infrastructure
+ * only; never linked into the CUDA library).
+ */
+#ifndef BURR_ORACLE_H
+#define BURR_ORACLE_H
+#include <stdint.h>
+
+#define OR_MAX_LAYERS 8
+#define OR_EINVAL (-1)
+#define OR_ENOMEM (-2)
+#define OR_UNSOLVABLE (-3)
+#define OR_FAIL (-4)
+
+typedef struct {
+    uint32_t r;                     /* value bits, 1..32 */
+    uint32_t w;                     /* ribbon width, 64 */
+    uint32_t B;                     /* bucket size in slots, 128 */
+    uint32_t levels[4];             /* 2-bit threshold levels in slots, {0,..,B} */
+    double alpha;                   /* keys per slot (overload when > 1) */
+    uint32_t layers;                /* bumping layers before the base case */
+    uint32_t fb_max_retries;        /* base-case retries */
+    uint64_t partition_slots;       /* P: cut every P start slots */
+    uint64_t min_partition_slots;   /* layers below this are one partition */
+    uint64_t seed;
+    double fb_slack;                /* base case m = n(1+slack)+w, x1.1 per retry */
+    uint64_t cut_P[OR_MAX_LAYERS];  /* per-layer override of P (0 = P) */
+} or_params;
+
+typedef struct {
+    uint64_t n, m, seed_index, nbuckets, nparts, part_slots, nbumped;
+    uint64_t *thresh;               /* ceil(nbuckets/32) words of 2-bit codes */
+    uint64_t *z;                    /* (m/64)*r words, interleaved bit planes */
+} or_layer;
+
+typedef struct {
+    or_params params;
+    uint64_t n;
+    uint64_t fb_attempt;
+    or_layer layer[OR_MAX_LAYERS + 1];  /* [OR_MAX_LAYERS] is the base case */
+} or_struct;
+
+typedef struct {
+    uint64_t xor_steps;             /* row XORs during elimination */
+    uint64_t inserted;              /* insertion attempts */
+    uint64_t max_drift;             /* max pivot - start */
+    uint64_t bumped[OR_MAX_LAYERS];
+} or_stats;
+
+uint64_t or_mix64(uint64_t z);
+uint64_t or_layer_seed(uint64_t seed, uint64_t index);
+void or_hash(uint64_t key, uint64_t sigma, uint64_t m, uint32_t w,
+             uint64_t *start, uint64_t *coeff);
+uint64_t or_layer_slots(uint64_t n, double alpha, uint32_t w);
+uint64_t or_fallback_slots(uint64_t n, double slack, uint32_t w, uint32_t attempt);
+uint64_t or_num_buckets(uint64_t m, uint32_t w, uint32_t B);
+uint64_t or_num_partitions(uint64_t m, uint64_t P, uint64_t min_slots);
+int or_forced_code(const uint32_t levels[4], uint32_t w);
+int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                   uint32_t r, uint64_t m, uint64_t sigma,
+                   const uint32_t levels[4], uint32_t B, uint32_t w,
+                   const uint64_t *cuts, uint64_t ncuts, int fallback,
+                   uint64_t *thresh, uint64_t *z,
+                   uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                   or_stats *st);
+void or_default_params(or_params *p);
+int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+             const or_params *p, or_struct *out, or_stats *st);
+void or_free(or_struct *s);
+uint32_t or_query_one(const or_struct *s, uint64_t key);
+void or_query(const or_struct *s, const uint64_t *keys, uint32_t *out, uint64_t n);
+uint64_t or_export(const or_struct *s, uint8_t *buf, uint64_t cap);
+double or_overhead(const or_struct *s);
+
+#endif

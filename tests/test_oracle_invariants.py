@@ -1,0 +1,113 @@
+"""Invariants of the whole layered structure, checked on the oracle.
+
+* query(x) = f(x) for every x in S (retrieval problem, Sec. 1);
+* on keys outside S the answer is arbitrary; for a filter (values = r-bit
+  fingerprints) it matches the fingerprint with probability 2^-r (Sec. 1);
+* the result does not depend on the input order (S is a set);
+* partitions are independent: building one partition alone gives the same
+  thresholds and table bits as building it inside its layer (Sec. 3);
+* a key set that is not a set (a duplicated key) cannot be solved: the base
+  case exhausts its retries (Sec. 4: the last layer is scaled up until it
+  solves, and never does here).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_12365_gb300 import inputs as I
+from tests.bruteforce import codes_of, unpack_z
+
+
+def _kv(n, r, seed=I.KEY_SEED):
+    k = I.keys_np(n, seed=seed)
+    return k, I.values_np(k, r).astype(np.uint32)
+
+
+@pytest.mark.parametrize("n,r,P", [(0, 8, 65536), (1, 8, 65536), (2, 1, 65536), (77, 3, 65536),
+                                   (5000, 8, 1024), (1 << 16, 8, 4096), (1 << 16, 16, 65536),
+                                   (20000, 32, 2048), (30000, 1, 4096)])
+def test_query_returns_stored_value(n, r, P):
+    k, v = _kv(n, r, seed=n * 31 + r)
+    s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=P)
+    assert s.ok
+    assert np.array_equal(s.query(k), v)
+
+
+def test_false_positive_rate_is_two_to_minus_r():
+    n, r = 1 << 16, 8
+    k, v = _kv(n, r)
+    s = O.build(k, v, r=r, partition_slots=4096, min_partition_slots=4096)
+    neg = I.keys_np(n, offset=n)                   # counters [n, 2n): disjoint from S
+    fp = I.values_np(neg, r).astype(np.uint32)
+    hits = int(np.sum(s.query(neg) == fp))
+    mean = n / 2 ** r
+    sd = math.sqrt(n * 2 ** -r * (1 - 2 ** -r))
+    assert abs(hits - mean) < 6 * sd
+
+
+def test_permutation_invariance():
+    n, r = 20000, 8
+    k, v = _kv(n, r)
+    a = O.build(k, v, r=r, partition_slots=2048, min_partition_slots=2048).export()
+    perm = np.random.default_rng(3).permutation(n)
+    b = O.build(k[perm], v[perm], r=r, partition_slots=2048, min_partition_slots=2048).export()
+    assert a == b
+
+
+def test_partition_alone_equals_partition_in_layer():
+    n, r, P = 12000, 8, 2048
+    k, v = _kv(n, r)
+    m = O.layer_slots(n, 1.015)
+    K = O.num_partitions(m, P, 0)
+    cuts = [j * P for j in range(1, K)]
+    sigma = O.layer_seed(17, 0)
+    full = O.build_layer(k, v, r, m, sigma, cuts=cuts)
+    nb = O.num_buckets(m)
+    zf = unpack_z(full.z, r, m)
+    cf = codes_of(full.thresh, nb)
+    starts = np.array([O.hash_key(int(x), sigma, m)[0] for x in k])
+    bounds = [0] + cuts + [m - 63]
+    own = [0] + [c + 64 for c in cuts] + [m]
+    for j in (0, 1, K // 2, K - 1):
+        sel = (starts >= bounds[j]) & (starts < bounds[j + 1])
+        alone = O.build_layer(k[sel], v[sel], r, m, sigma, cuts=cuts)
+        za = unpack_z(alone.z, r, m)
+        ca = codes_of(alone.thresh, nb)
+        assert za[own[j]:own[j + 1]] == zf[own[j]:own[j + 1]]
+        b0, b1 = bounds[j] // 128, (bounds[j + 1] + 127) // 128
+        assert ca[b0:b1] == cf[b0:b1]
+        assert sorted(alone.bumped_keys.tolist()) == sorted(
+            x for x in full.bumped_keys.tolist() if bounds[j] <= O.hash_key(int(x), sigma, m)[0] < bounds[j + 1])
+
+
+def test_single_partition_when_layer_is_small():
+    # minimum partition size (minbpt analogue, Sec. 3): below it no cut is made
+    n, r = 3000, 8
+    k, v = _kv(n, r)
+    a = O.build(k, v, r=r, partition_slots=1024, min_partition_slots=1 << 20)
+    b = O.build(k, v, r=r, partition_slots=1 << 20, min_partition_slots=0)
+    assert a.layer(0)["nparts"] == 1 and a.export()[200:] == b.export()[200:]
+
+
+def test_duplicate_key_is_unsolvable():
+    k, v = _kv(1000, 8)
+    k[10] = k[20]
+    v[10] = v[20]
+    s = O.build(k, v, r=8, fb_max_retries=3)
+    assert s.status == O.UNSOLVABLE
+
+
+def test_empty_input():
+    s = O.build(np.zeros(0, np.uint64), np.zeros(0, np.uint32), r=8)
+    assert s.ok and s.layer(0)["m"] == 0 and s.layer("fallback")["m"] == 0
+    assert s.query(I.keys_np(10)).tolist() == [0] * 10
+
+
+def test_invalid_params_rejected():
+    k, v = _kv(10, 8)
+    for bad in (dict(r=0), dict(r=33), dict(w=32), dict(partition_slots=100),
+                dict(levels=(0, 32, 64, 100)), dict(levels=(0, 32, 32, 128)),
+                dict(levels=(5, 32, 64, 128)), dict(alpha=0.0)):
+        assert O.build(k, v, **bad).status == O.EINVAL
