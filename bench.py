@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 BuRR hot path: one step = build a BuRR structure of n
+keys (hash, sort by bucket, band + bump with partition cuts, back-substitution,
+recursion into the next layers and the base case) and query n keys (half of
+them members, half not), all through the C ABI of libburr.so.
+
+Default workload: 10^8 uniform-random 64-bit keys, r = 8 (8-bit filter
+values), w = 64, partitions of 2^16 slots, plus 10^8 queries.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl burr|reference]
+
+Prints one JSON line (rank 0).  `value` is keys per second through the whole
+step, device-resident inputs; `e2e` is the same with the inputs in pinned host
+memory and the copies inside the timed region; `roofline` is the dominant
+kernel (layer-0 band + bump) against the measured HBM bandwidth;
+`cpu_baseline` is the serial CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BuRR construction Mkeys/s and % HBM roofline at 1 GB300 (plain vs batched/served)"
+UNIT = "Mkeys/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="burr", choices=["burr", "reference"])
+    ap.add_argument("--n", type=int, default=100_000_000)
+    ap.add_argument("--r", type=int, default=8)
+    ap.add_argument("--partition-slots", type=int, default=65536)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 22, help="keys of the oracle sample")
+    ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per reference-arm step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-steps", action="store_true",
+                    help="only run warmup+steps (for ncu launch lists), skip extras")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel_src: str):
+    """Per-launch DRAM bytes of the layer-0 band launch from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_band_1e8_r8_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if kv.get("kernel_source_sha256_16") != src_hash:
+            return None
+        return float(kv["dram_bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n_s: int, r: int, P: int):
+    """Serial CPU oracle: build + query of n_s keys; returns (seconds, n_s)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2411_12365_gb300 import inputs as I
+    k = I.keys_np(n_s)
+    v = I.values_np(k, r).astype(np.uint32)
+    q = np.concatenate([k[: n_s // 2], I.keys_np(n_s - n_s // 2, offset=n_s)])
+    t0 = time.perf_counter()
+    s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=P)
+    out = s.query(q)
+    dt = time.perf_counter() - t0
+    assert s.ok and np.array_equal(out[: n_s // 2], v[: n_s // 2])
+    return dt
+
+
+def run_reference(a, ws, rank, pg):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build_lib()
+    n_s = a.ref_sample
+    for _ in range(a.warmup):
+        oracle_sample(n_s, a.r, a.partition_slots)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle_sample(n_s, a.r, a.partition_slots)
+    dt = (time.perf_counter() - t0) / a.steps
+    value = n_s / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"serial C oracle: build + query of {n_s} keys per step (of the {a.n}-key workload)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(a):
+    return {"workload": f"{a.n} uniform-random 64-bit keys, r={a.r}, w=64, 2-bit thresholds, "
+                        f"partition size {a.partition_slots} slots, plain build + {a.n} queries "
+                        f"(half members, half non-members)",
+            "n_keys": a.n, "queries": a.n, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
+            "partition_slots": a.partition_slots, "load_factor": 1.015, "layers": 4,
+            "l2_flush": "inputs larger than L2 (keys 8n bytes)", "parallelism": "one independent structure per GPU"}
+
+
+def main():
+    a = args_()
+    ws, rank, local, pg = dist_setup()
+    if a.impl == "reference":
+        run_reference(a, ws, rank, pg)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2411_12365_gb300 import burr
+    from paper_2411_12365_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, r, P = a.n, a.r, a.partition_slots
+    vb = 1 if r <= 8 else (2 if r <= 16 else 4)
+    seed = I.KEY_SEED + rank * 0x100000000        # independent structure per rank
+    keys = I.keys_torch(n, dev, seed=seed)
+    vals = I.values_torch(keys, r)
+    half = n // 2
+    qkeys = torch.cat([keys[:half], I.keys_torch(n - half, dev, seed=seed, offset=n)])
+    qout = torch.empty(n, dtype=burr.value_torch_dtype(r), device=dev)
+    params = burr.default_params(partition_slots=P, min_partition_slots=P, flags=burr.FLAG_TIMING)
+    torch.cuda.synchronize()
+
+    stats_acc = []
+    launches = [0]
+
+    def step():
+        h = burr.build(keys, vals, r, params=params)
+        h.query(qkeys, out=qout)
+        st = h.stats()
+        stats_acc.append(st)
+        launches[0] += st["kernel_launches"] + 1
+        h.free()
+
+    for _ in range(a.warmup):
+        step()
+    # correctness of the timed configuration
+    assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
+    stats_acc.clear()
+    launches[0] = 0
+    torch.cuda.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        ev0.record()
+        for _ in range(a.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    barrier(pg)
+    ms = ev0.elapsed_time(ev1) / a.steps
+    ms = max_over_ranks(pg, ms)
+    value = ws * n / (ms / 1e3) / 1e6
+    if a.profile_steps:
+        if rank == 0:
+            print(json.dumps({"ms_per_step": ms, "value": value}))
+        return
+
+    # per-stage device times (layer 0 dominates)
+    st0 = stats_acc[-1]
+    layers = st0["layers"]
+    avg = lambda f: statistics.mean(f(s) for s in stats_acc)  # noqa: E731
+    band0 = avg(lambda s: s["stage_ms"][0][1])
+    sort0 = avg(lambda s: s["stage_ms"][0][0])
+    bs0 = avg(lambda s: s["stage_ms"][0][2])
+    build_ms = avg(lambda s: s["total_ms"])
+    n0, m0 = st0["layer_n"][0], st0["layer_m"][0]
+    nb0 = (m0 - 64 + 128) // 128
+    bump0 = st0["layer_bumped"][0]
+    band_bytes = n0 * (8 + vb) + (nb0 + 1) * 4 + m0 * (8 + vb) + bump0 * (8 + vb) + ((nb0 + 31) // 32) * 8
+    peak, peak_kind = measured_peaks()
+    achieved = band_bytes / (band0 / 1e3) / 1e9
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
+    # space overhead (bits of tables + thresholds over r*n)
+    bits = sum(st0["layer_m"][l] * r + 2 * ((st0["layer_m"][l] - 64 + 128) // 128 if st0["layer_m"][l] else 0)
+               for l in range(layers)) + st0["layer_m"][layers] * r
+    overhead = bits / (r * n) - 1
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": workload_config(a), "wall_s_timed": wall,
+        "breakdown": {
+            "build_ms": build_ms, "query_ms": ms - build_ms,
+            "build_mkeys_s": n / build_ms / 1e3, "query_mkeys_s": n / max(ms - build_ms, 1e-9) / 1e3,
+            "layer0_ms": {"sort(4 kernels)": sort0, "band_bump": band0, "backsub": bs0},
+            "stage_ms_per_layer": [[round(x, 4) for x in s] for s in st0["stage_ms"]],
+            "layer_n": st0["layer_n"], "layer_m": st0["layer_m"], "layer_parts": st0["layer_parts"],
+            "space_overhead": overhead,
+            "paper_cpu_context": "67.8 Mkeys/s construction, 1e8 keys, 64 threads on EPYC 7551P (Fig. 7)",
+        },
+        "roofline": {"bound": "hbm", "kernel": "k_band (layer 0)", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes": band_bytes,
+                     "note": "band+bump is latency-bound (dependent GF(2) elimination chains)"},
+        "gpu_launches": launches[0],
+    }
+    line["clocks"] = clk.summary()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    if not a.no_e2e:
+        hk = keys.cpu().pin_memory()
+        hv = vals.cpu().pin_memory()
+        hq = qkeys.cpu().pin_memory()
+        ho = torch.empty(n, dtype=qout.dtype).pin_memory()
+        hk_np, hv_np, hq_np, ho_np = hk.numpy(), hv.numpy(), hq.numpy(), ho.numpy()
+        p2 = burr.default_params(partition_slots=P, min_partition_slots=P)
+
+        def e2e_step():
+            h = burr.build(hk_np, hv_np, r, params=p2)
+            h.query(hq_np, out=ho_np)
+            h.free()
+
+        for _ in range(max(1, min(a.warmup, 2))):
+            e2e_step()
+        assert np.array_equal(ho_np[:half], hv_np[:half])
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / a.steps)
+        line["e2e"] = {"value": ws * n / e2e_s / 1e6, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                       "h2d_bytes_per_step": n * 8 + n * vb + n * 8, "d2h_bytes_per_step": n * vb}
+
+    if not a.no_cpu and rank == 0:
+        dt = oracle_sample(a.cpu_sample, r, P)
+        line["cpu_baseline"] = {"value": a.cpu_sample / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"serial C oracle: build + query of {a.cpu_sample} keys "
+                                          f"(same r, P, load; {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

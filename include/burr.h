@@ -1,0 +1,193 @@
+/*
+ * burr.h -- C ABI of libburr.so: GB300 (sm_103a) construction and query of
+ * Bumped Ribbon Retrieval (BuRR) with partitioned parallel construction.
+ *
+ * The problem (Sec. 1 and the abstract of "Brief Announcement: Parallel
+ * Construction of Bumped Ribbon Retrieval"): store a static function
+ * f: S -> {0,1}^r for a set S of 64-bit keys so that a query of x in S returns
+ * f(x); a query of x outside S returns an arbitrary (here: deterministic)
+ * r-bit value.  The structure does not store S.
+ *
+ * Method (Sec. 2 and 3):
+ *   - each key is one GF(2) equation: a 64-bit coefficient row starting at a
+ *     hashed start slot of a layer of m slots (ribbon width w = 64);
+ *   - equations are sorted by start slot and eliminated bucket by bucket
+ *     (128 start slots per bucket); where elimination fails, a prefix of the
+ *     bucket is bumped to the next layer and the bucket's 2-bit threshold
+ *     (one of four levels) records it;
+ *   - each layer is cut into independent partitions of P start slots; the
+ *     first bucket of every partition after the first bumps its first 64
+ *     offsets so that no kept equation overlaps a cut, which makes the
+ *     partitions independent and the cuts invisible to queries;
+ *   - back-substitution (free slots fixed to 0) gives the table Z;
+ *   - bumped keys form the next layer; after `layers` layers a base case
+ *     without bumping is retried with a new seed and 10% more slots until it
+ *     solves.
+ *
+ * Conventions the paper leaves open (hash function, levels, load factor,
+ * storage layout) are fixed here as the library's specification:
+ *   mix(z)       SplitMix64 output function (Steele, Lea, Flood 2014)
+ *   sigma_l      mix(seed ^ ((l+1) * 0x9E3779B97F4A7C15)), l = layer index
+ *                (bumping layers 0..layers-1, base-case attempt a: layers+a)
+ *   h            mix(key ^ sigma_l)
+ *   start        floor(h * (m - 63) / 2^64)
+ *   coefficients mix(h + sigma_l) | 1   (bit k <-> slot start+k)
+ *   bucket       start / 128, offset = start % 128; keys with
+ *                offset < levels[code] are bumped
+ *   layer slots  m = align64(ceil(n / load_factor) + 64)
+ *   partitions   K = 1 if m < max(P, min_partition_slots), else floor(m/P);
+ *                cut j at start slot j*P, the last partition takes the rest;
+ *                partition j owns slots [j*P + 64, (j+1)*P + 64)
+ *   table layout per 64-slot block, r 64-bit words; bit k of slot s is bit
+ *                s%64 of word (s/64)*r + k
+ *   thresholds   2-bit codes, 32 per 64-bit word, bucket b in bits
+ *                [2(b%32), 2(b%32)+2) of word b/32
+ *
+ * Pointers: every key/value/output pointer may be host memory (pageable or
+ * pinned) or device memory of the current device; the library detects which.
+ * Values are unsigned integers of the smallest width holding r bits
+ * (uint8 for r <= 8, uint16 for r <= 16, uint32 for r <= 32); bits at and
+ * above r are ignored.  Queries write the same type.
+ *
+ * Errors: every call returns 0 or a negative BURR_ERR_* code; nothing throws
+ * across the ABI.  burr_last_error() gives a message for the calling thread.
+ */
+#ifndef BURR_H
+#define BURR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BURR_OK 0
+#define BURR_ERR_INVALID (-1)     /* bad argument or parameter */
+#define BURR_ERR_OOM (-2)         /* device allocation failed */
+#define BURR_ERR_UNSOLVABLE (-3)  /* base case failed every retry (e.g. duplicate keys) */
+#define BURR_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired */
+#define BURR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define BURR_ERR_INTERNAL (-6)    /* a device-side capacity check tripped */
+
+#define BURR_THRESH_2BIT 0u
+#define BURR_MAX_LAYERS 8
+#define BURR_FLAG_TIMING 1u       /* record per-stage device times (burr_stats) */
+
+typedef struct burr_handle burr_handle;
+
+/* Construction parameters (Sec. 2-4; defaults from burr_default_params). */
+typedef struct {
+    uint32_t ribbon_width;          /* w: must be 64 */
+    uint32_t bucket_slots;          /* B: start slots per bucket, 64 or 128 (128) */
+    uint32_t threshold_mode;        /* BURR_THRESH_2BIT */
+    uint32_t layers;                /* bumping layers before the base case, 0..8 (4) */
+    uint32_t levels[4];             /* threshold levels in slots: 0 < l1 < l2 < B = l3 ({0,32,64,128});
+                                       the smallest level >= w is the level forced after a cut */
+    double load_factor;             /* keys per slot of a bumping layer (1.015) */
+    uint64_t partition_slots;       /* P: start slots per partition, a multiple of B (65536) */
+    uint64_t min_partition_slots;   /* layers with fewer slots are one partition (65536) */
+    uint64_t seed;                  /* hash seed */
+    double fallback_slack;          /* base case m = align64(ceil(n (1+slack)) + 64) (0.1) */
+    uint32_t fallback_max_retries;  /* base-case retries, each with 10% more slots (16) */
+    uint32_t flags;                 /* BURR_FLAG_* */
+} burr_params;
+
+/* Per-build statistics. */
+typedef struct {
+    uint64_t n;                                 /* keys */
+    uint32_t r;
+    uint32_t layers;                            /* bumping layers configured */
+    uint64_t layer_n[BURR_MAX_LAYERS + 1];      /* keys per layer; [layers] = base case */
+    uint64_t layer_m[BURR_MAX_LAYERS + 1];      /* slots per layer */
+    uint64_t layer_parts[BURR_MAX_LAYERS + 1];  /* partitions per layer */
+    uint64_t layer_bumped[BURR_MAX_LAYERS + 1]; /* keys bumped out of each layer */
+    uint32_t fallback_attempt;                  /* base-case attempt that solved */
+    uint32_t pad;
+    /* device milliseconds per layer and stage (BURR_FLAG_TIMING):
+       [l][0] sort, [l][1] band+bump, [l][2] back-substitution */
+    float stage_ms[BURR_MAX_LAYERS + 1][3];
+    float total_ms;                             /* whole build, device time */
+    float pad2;
+    uint64_t table_bytes;                       /* Z + thresholds of all layers */
+    uint64_t kernel_launches;                   /* CUDA kernels this build launched */
+} burr_stats_t;
+
+/* Fill *p with the defaults above.  Returns BURR_OK or BURR_ERR_INVALID (p NULL). */
+int burr_default_params(burr_params *p);
+
+/*
+ * Build the structure for n keys (distinct; S is a set) and their r-bit values.
+ *   keys    n uint64 keys, host or device, caller-owned, read only.
+ *   values  n values of the r-bit value type, host or device, caller-owned.
+ *   r       value bits, 1..32.
+ *   p       parameters (NULL = defaults).
+ *   stream  cudaStream_t the work is ordered on (NULL = legacy default stream).
+ *   out     receives a handle owned by the library until burr_free.
+ * The call returns when the handle is complete (it synchronises the stream
+ * once per layer to size the next layer).  n = 0 gives a valid empty handle.
+ * Errors: BURR_ERR_INVALID (bad arguments / parameters / m >= 2^32),
+ * BURR_ERR_OOM, BURR_ERR_UNSOLVABLE, BURR_ERR_INTERNAL, BURR_ERR_CUDA.
+ */
+int burr_build(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
+               const burr_params *p, void *stream, burr_handle **out);
+
+/*
+ * Query n keys (host or device), writing n values of the handle's value type
+ * to out (host or device).  Stream-ordered: with device keys and output the
+ * call only enqueues work on `stream`; with any host pointer it copies through
+ * device buffers and returns after the results are in `out`.
+ */
+int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n, void *stream);
+
+/* Bytes of the device tables (Z of every layer + thresholds + a 64-byte header). */
+int burr_size_bytes(const burr_handle *h, uint64_t *bytes);
+
+/*
+ * Canonical little-endian serialisation (checkpoint format and the form in
+ * which results are compared bit for bit):
+ *   u32 magic 0x52525542, u32 version 1, u32 r, u32 w, u32 B, u32 layers,
+ *   u32 levels[4], u64 seed, u64 bits of load_factor, u64 n, u64 partition_slots,
+ *   per bumping layer: u64 n, m, partitions, buckets, bumped;
+ *   base case: u64 n, m, seed index, attempt;
+ *   per bumping layer: threshold words (ceil(buckets/32) u64), table words
+ *   ((m/64)*r u64); base-case table words.
+ * If host_buf is NULL or *len is too small, *len is set to the size needed and
+ * BURR_ERR_INVALID is returned; otherwise *len = bytes written.
+ */
+int burr_export(const burr_handle *h, void *host_buf, uint64_t *len);
+
+int burr_stats(const burr_handle *h, burr_stats_t *st);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void burr_free(burr_handle *h);
+
+const char *burr_strerror(int code);
+const char *burr_last_error(void);
+
+/*
+ * Stage entry points, exposed so that each stage of the build can be checked
+ * against an independent implementation.  All pointers are device memory.
+ *
+ * burr_stage_hash: step "hash each key to (start slot, coefficient row)" of
+ * one layer (Sec. 2, Fig. 1): for i < n, start[i] and coeff[i] of keys[i] in a
+ * layer of m slots with hash layer index `layer_index` and seed `seed`.
+ */
+int burr_stage_hash(const uint64_t *d_keys, uint64_t n, uint64_t seed, uint32_t layer_index,
+                    uint64_t m, uint32_t *d_start, uint64_t *d_coeff, void *stream);
+
+/*
+ * burr_stage_sort: step "sort the equations by start slot" (Sec. 4, sorting by
+ * insertion position) as the build does it: keys and values grouped by bucket
+ * (start/128) in ascending bucket order, any order inside a bucket.
+ * d_bucket_start receives buckets+1 offsets (buckets = (m - 64 + 128)/128).
+ * Scratch is allocated on `stream` and released before return.
+ */
+int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, uint32_t r,
+                    uint64_t seed, uint32_t layer_index, uint64_t m,
+                    uint64_t *d_sorted_keys, void *d_sorted_values, uint32_t *d_bucket_start,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BURR_H */

@@ -78,6 +78,13 @@ void or_hash(uint64_t key, uint64_t sigma, uint64_t m, uint32_t w,
     *coeff = or_mix64(h + sigma) | 1ULL;
 }
 
+/* or_hash over an array of keys. */
+void or_hash_batch(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t m, uint32_t w,
+                   uint64_t *starts, uint64_t *coeffs)
+{
+    for (uint64_t i = 0; i < n; i++) or_hash(keys[i], sigma, m, w, &starts[i], &coeffs[i]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sizing and partitioning (READING: overload factor and cut placement).     */
 /* ------------------------------------------------------------------------ */
@@ -507,7 +514,7 @@ uint64_t or_export(const or_struct *s, uint8_t *buf, uint64_t cap)
     for (int i = 0; i < 4; i++) q = put32(q, p->levels[i]);
     uint64_t abits; memcpy(&abits, &p->alpha, 8);
     q = put64(q, p->seed); q = put64(q, abits); q = put64(q, s->n);
-    q = put64(q, 0);
+    q = put64(q, p->partition_slots);
     for (uint32_t l = 0; l < p->layers; l++) {
         const or_layer *L = &s->layer[l];
         q = put64(q, L->n); q = put64(q, L->m); q = put64(q, L->nparts);

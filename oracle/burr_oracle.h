@@ -51,6 +51,8 @@ uint64_t or_mix64(uint64_t z);
 uint64_t or_layer_seed(uint64_t seed, uint64_t index);
 void or_hash(uint64_t key, uint64_t sigma, uint64_t m, uint32_t w,
              uint64_t *start, uint64_t *coeff);
+void or_hash_batch(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t m, uint32_t w,
+                   uint64_t *starts, uint64_t *coeffs);
 uint64_t or_layer_slots(uint64_t n, double alpha, uint32_t w);
 uint64_t or_fallback_slots(uint64_t n, double slack, uint32_t w, uint32_t attempt);
 uint64_t or_num_buckets(uint64_t m, uint32_t w, uint32_t B);

@@ -81,6 +81,8 @@ def lib():
             L.or_layer_seed.restype = u64; L.or_layer_seed.argtypes = [u64, u64]
             L.or_hash.restype = None
             L.or_hash.argtypes = [u64, u64, u64, u32, C.POINTER(u64), C.POINTER(u64)]
+            L.or_hash_batch.restype = None
+            L.or_hash_batch.argtypes = [p, u64, u64, u64, u32, p, p]
             L.or_layer_slots.restype = u64; L.or_layer_slots.argtypes = [u64, C.c_double, u32]
             L.or_fallback_slots.restype = u64
             L.or_fallback_slots.argtypes = [u64, C.c_double, u32, u32]
@@ -130,6 +132,15 @@ def hash_key(key: int, sigma: int, m: int, w: int = 64):
     s, c = C.c_uint64(), C.c_uint64()
     lib().or_hash(key, sigma, m, w, C.byref(s), C.byref(c))
     return int(s.value), int(c.value)
+
+
+def hash_many(keys, sigma: int, m: int, w: int = 64):
+    """(starts, coeffs) of every key, as uint64 arrays."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    s = np.empty(len(keys), dtype=np.uint64)
+    c = np.empty(len(keys), dtype=np.uint64)
+    lib().or_hash_batch(_ptr(keys), len(keys), sigma, m, w, _ptr(s), _ptr(c))
+    return s, c
 
 
 def layer_slots(n, alpha, w=64):

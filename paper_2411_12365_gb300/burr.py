@@ -1,0 +1,236 @@
+"""Thin Python binding of libburr.so (include/burr.h): argument marshalling only.
+
+Every step of construction and query runs in the library's CUDA kernels.
+Inputs may be torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are
+passed as device pointers together with torch's current CUDA stream.  If the
+library has not been built, every call raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+BURR_OK = 0
+ERR_INVALID, ERR_OOM, ERR_UNSOLVABLE, ERR_TIMEOUT, ERR_CUDA, ERR_INTERNAL = -1, -2, -3, -4, -5, -6
+MAX_LAYERS = 8
+FLAG_TIMING = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BurrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"burr error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("ribbon_width", C.c_uint32), ("bucket_slots", C.c_uint32), ("threshold_mode", C.c_uint32),
+        ("layers", C.c_uint32), ("levels", C.c_uint32 * 4), ("load_factor", C.c_double),
+        ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64), ("seed", C.c_uint64),
+        ("fallback_slack", C.c_double), ("fallback_max_retries", C.c_uint32), ("flags", C.c_uint32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint64), ("r", C.c_uint32), ("layers", C.c_uint32),
+        ("layer_n", C.c_uint64 * (MAX_LAYERS + 1)), ("layer_m", C.c_uint64 * (MAX_LAYERS + 1)),
+        ("layer_parts", C.c_uint64 * (MAX_LAYERS + 1)), ("layer_bumped", C.c_uint64 * (MAX_LAYERS + 1)),
+        ("fallback_attempt", C.c_uint32), ("pad", C.c_uint32),
+        ("stage_ms", (C.c_float * 3) * (MAX_LAYERS + 1)), ("total_ms", C.c_float), ("pad2", C.c_float),
+        ("table_bytes", C.c_uint64), ("kernel_launches", C.c_uint64),
+    ]
+
+
+EXPORTED = ["burr_default_params", "burr_build", "burr_query", "burr_size_bytes", "burr_export",
+            "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
+            "burr_stage_sort"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libburr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libburr.so not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        p, u64, u32, i = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+        L.burr_default_params.argtypes = [C.POINTER(Params)]
+        L.burr_default_params.restype = i
+        L.burr_build.argtypes = [p, p, u64, u32, C.POINTER(Params), p, C.POINTER(p)]
+        L.burr_build.restype = i
+        L.burr_query.argtypes = [p, p, p, u64, p]
+        L.burr_query.restype = i
+        L.burr_size_bytes.argtypes = [p, C.POINTER(u64)]
+        L.burr_size_bytes.restype = i
+        L.burr_export.argtypes = [p, p, C.POINTER(u64)]
+        L.burr_export.restype = i
+        L.burr_stats.argtypes = [p, C.POINTER(Stats)]
+        L.burr_stats.restype = i
+        L.burr_free.argtypes = [p]
+        L.burr_free.restype = None
+        L.burr_strerror.argtypes = [i]
+        L.burr_strerror.restype = C.c_char_p
+        L.burr_last_error.argtypes = []
+        L.burr_last_error.restype = C.c_char_p
+        L.burr_stage_hash.argtypes = [p, u64, u64, u32, u64, p, p, p]
+        L.burr_stage_hash.restype = i
+        L.burr_stage_sort.argtypes = [p, p, u64, u32, u64, u32, u64, p, p, p, p]
+        L.burr_stage_sort.restype = i
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != BURR_OK:
+        L = load()
+        raise BurrError(rc, f"{L.burr_strerror(rc).decode()}: {L.burr_last_error().decode()}")
+
+
+def value_np_dtype(r: int):
+    return np.uint8 if r <= 8 else (np.uint16 if r <= 16 else np.uint32)
+
+
+def value_torch_dtype(r: int):
+    import torch
+    return torch.uint8 if r <= 8 else (torch.int16 if r <= 16 else torch.int32)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(load().burr_default_params(C.byref(p)))
+    for k, v in kw.items():
+        if k == "levels":
+            p.levels = (C.c_uint32 * 4)(*v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr_and_stream(x, stream):
+    """(pointer, stream handle, keepalive) for a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                x = x.contiguous()
+            if x.is_cuda:
+                s = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
+                return x.data_ptr(), s, x
+            return x.data_ptr(), stream, x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, stream, a
+
+
+def _stream_value(s):
+    if s is None:
+        return None
+    return getattr(s, "cuda_stream", s)
+
+
+class Handle:
+    """A built structure owned by the library (freed by .free() or GC)."""
+
+    def __init__(self, ptr, r):
+        self._h = C.c_void_p(ptr)
+        self.r = r
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().burr_free(self._h)
+            self._h = C.c_void_p(None)
+
+    def query(self, keys, out=None, stream=None):
+        """Values of `keys` (torch CUDA/CPU tensor or numpy array), same kind back."""
+        kp, st, keep = _ptr_and_stream(keys, _stream_value(stream))
+        n = int(keep.numel() if hasattr(keep, "numel") else keep.size)
+        if out is None:
+            if hasattr(keep, "numel"):
+                import torch
+                out = torch.empty(n, dtype=value_torch_dtype(self.r), device=keep.device)
+            else:
+                out = np.empty(n, dtype=value_np_dtype(self.r))
+        op, _, okeep = _ptr_and_stream(out, st)
+        _check(load().burr_query(self._h, kp, op, n, st))
+        return okeep
+
+    def export(self) -> bytes:
+        L = load()
+        need = C.c_uint64(0)
+        L.burr_export(self._h, None, C.byref(need))
+        buf = (C.c_uint8 * need.value)()
+        ln = C.c_uint64(need.value)
+        _check(L.burr_export(self._h, buf, C.byref(ln)))
+        return bytes(buf[:ln.value])
+
+    def size_bytes(self) -> int:
+        b = C.c_uint64(0)
+        _check(load().burr_size_bytes(self._h, C.byref(b)))
+        return b.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().burr_stats(self._h, C.byref(s)))
+        nl = s.layers + 1
+        return dict(n=s.n, r=s.r, layers=s.layers, layer_n=list(s.layer_n[:nl]), layer_m=list(s.layer_m[:nl]),
+                    layer_parts=list(s.layer_parts[:nl]), layer_bumped=list(s.layer_bumped[:nl]),
+                    fallback_attempt=s.fallback_attempt,
+                    stage_ms=[list(s.stage_ms[l]) for l in range(nl)], total_ms=s.total_ms,
+                    table_bytes=s.table_bytes, kernel_launches=s.kernel_launches)
+
+
+def build(keys, values, r: int, params: Params | None = None, stream=None, **kw) -> Handle:
+    """burr_build: keys uint64 (int64 tensors hold the same bits), values of the r-bit type."""
+    if params is None:
+        params = default_params(**kw)
+    kp, st, kk = _ptr_and_stream(keys, _stream_value(stream))
+    vp, _, vk = _ptr_and_stream(values, st)
+    n = int(kk.numel() if hasattr(kk, "numel") else kk.size)
+    out = C.c_void_p()
+    _check(load().burr_build(kp, vp, n, r, C.byref(params), st, C.byref(out)))
+    return Handle(out.value, r)
+
+
+def stage_hash(keys, seed: int, layer_index: int, m: int, stream=None):
+    """Stage entry point: (start uint32 as int32, coeff uint64 as int64) CUDA tensors."""
+    import torch
+    n = keys.numel()
+    start = torch.empty(n, dtype=torch.int32, device=keys.device)
+    coeff = torch.empty(n, dtype=torch.int64, device=keys.device)
+    kp, st, _ = _ptr_and_stream(keys, _stream_value(stream))
+    _check(load().burr_stage_hash(kp, n, seed, layer_index, m, start.data_ptr(), coeff.data_ptr(), st))
+    return start, coeff
+
+
+def stage_sort(keys, values, r: int, seed: int, layer_index: int, m: int, stream=None):
+    """Stage entry point: keys/values grouped by bucket plus bucket offsets."""
+    import torch
+    n = keys.numel()
+    nb = (m - 64 + 128) // 128
+    sk = torch.empty_like(keys)
+    sv = torch.empty_like(values)
+    bs = torch.empty(nb + 1, dtype=torch.int32, device=keys.device)
+    kp, st, _ = _ptr_and_stream(keys, _stream_value(stream))
+    _check(load().burr_stage_sort(kp, values.data_ptr(), n, r, seed, layer_index, m, sk.data_ptr(),
+                                  sv.data_ptr(), bs.data_ptr(), st))
+    return sk, sv, bs

@@ -1,0 +1,608 @@
+// burr_api.cu -- host side of libburr.so: parameter checks, the layer driver
+// (Sec. 2 layers, Sec. 3 partitions and base case), handles, query dispatch,
+// export and statistics.  Every step of the method runs in the kernels of
+// burr_sort.cu, burr_band.cu and burr_query.cu; this file only sizes layers,
+// allocates, launches and reads back one counter per layer.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "burr_internal.cuh"
+
+using namespace burr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(BURR_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(BURR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+uint32_t value_bytes(uint32_t r) { return r <= 8 ? 1u : (r <= 16 ? 2u : 4u); }
+uint64_t align64(uint64_t x) { return (x + 63) & ~63ull; }
+
+uint64_t layer_slots(uint64_t n, double alpha) {
+    if (n == 0) return 0;
+    return align64((uint64_t)std::ceil((double)n / alpha) + kW);
+}
+
+uint64_t fallback_slots(uint64_t n, double slack, uint32_t attempt) {
+    if (n == 0) return 0;
+    uint64_t m = align64((uint64_t)std::ceil((double)n * (1.0 + slack)) + kW);
+    for (uint32_t a = 0; a < attempt; ++a) m = align64((uint64_t)std::ceil((double)m * 1.1));
+    return m;
+}
+
+uint64_t num_buckets(uint64_t m, uint32_t B) { return m == 0 ? 0 : (m - kW + B) / B; }
+
+uint64_t num_partitions(uint64_t m, uint64_t P, uint64_t minP) {
+    if (m == 0) return 0;
+    if (m < minP || m < P) return 1;
+    return m / P;
+}
+
+int forced_code(const uint32_t lv[4]) {
+    for (int i = 0; i < 4; ++i)
+        if (lv[i] >= kW) return i;
+    return -1;
+}
+
+int validate(const burr_params &p, uint32_t r) {
+    if (r < 1 || r > 32) return fail(BURR_ERR_INVALID, "r=%u outside [1,32]", r);
+    if (p.ribbon_width != kW) return fail(BURR_ERR_INVALID, "ribbon_width must be 64");
+    if (p.bucket_slots != 64 && p.bucket_slots != 128)
+        return fail(BURR_ERR_INVALID, "bucket_slots must be 64 or 128");
+    if (p.threshold_mode != BURR_THRESH_2BIT) return fail(BURR_ERR_INVALID, "only 2-bit thresholds");
+    if (p.layers > BURR_MAX_LAYERS) return fail(BURR_ERR_INVALID, "layers > %d", BURR_MAX_LAYERS);
+    if (!(p.levels[0] == 0 && p.levels[0] < p.levels[1] && p.levels[1] < p.levels[2] &&
+          p.levels[2] < p.levels[3] && p.levels[3] == p.bucket_slots))
+        return fail(BURR_ERR_INVALID, "levels must be 0 < l1 < l2 < bucket_slots");
+    if (forced_code(p.levels) < 0) return fail(BURR_ERR_INVALID, "no level >= ribbon width");
+    if (!(p.load_factor > 0.0) || !std::isfinite(p.load_factor))
+        return fail(BURR_ERR_INVALID, "load_factor must be positive");
+    if (p.partition_slots == 0 || p.partition_slots % p.bucket_slots != 0)
+        return fail(BURR_ERR_INVALID, "partition_slots must be a positive multiple of bucket_slots");
+    if (!(p.fallback_slack >= 0.0) || !std::isfinite(p.fallback_slack))
+        return fail(BURR_ERR_INVALID, "fallback_slack must be >= 0");
+    return BURR_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void keep_pool_memory() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = true;
+}
+
+// Stream-ordered device allocations released together.
+struct Arena {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Arena(cudaStream_t s) : st(s) {}
+    cudaError_t alloc(void **p, size_t bytes) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 256;
+        cudaError_t e = cudaMallocAsync(p, bytes, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release(void *p) {
+        for (auto &q : ptrs)
+            if (q == p) {
+                cudaFreeAsync(q, st);
+                q = nullptr;
+            }
+    }
+    ~Arena() {
+        for (void *p : ptrs)
+            if (p) cudaFreeAsync(p, st);
+    }
+};
+
+struct LayerStore {
+    uint64_t n = 0, m = 0, nb = 0, K = 0, nbumped = 0, seed_index = 0, sigma = 0;
+    uint64_t *thresh = nullptr;   // ceil(nb/32) words (bumping layers)
+    uint64_t *z = nullptr;        // (m/64)*r words
+};
+
+}  // namespace
+
+struct burr_handle {
+    burr_params p;
+    uint32_t r = 0, vbytes = 0;
+    uint64_t n = 0;
+    LayerStore L[BURR_MAX_LAYERS + 1];
+    uint32_t fb_attempt = 0;
+    float stage_ms[BURR_MAX_LAYERS + 1][3] = {};
+    float total_ms = 0;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+void free_layers(burr_handle *h) {
+    for (auto &S : h->L) {
+        if (S.thresh) cudaFree(S.thresh);
+        if (S.z) cudaFree(S.z);
+        S.thresh = S.z = nullptr;
+    }
+}
+
+LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, uint64_t sigma, uint64_t K,
+                    bool fallback) {
+    LayerDesc L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.m = m;
+    L.range = m >= kW ? m - kW + 1 : 0;
+    L.sigma = sigma;
+    L.nb = num_buckets(m, p.bucket_slots);
+    L.P = fallback ? (m ? m : 1) : p.partition_slots;
+    L.K = (uint32_t)K;
+    L.r = r;
+    L.B = p.bucket_slots;
+    L.fallback = fallback ? 1u : 0u;
+    for (int i = 0; i < 4; ++i) L.levels[i] = p.levels[i];
+    L.forced_code = (uint32_t)forced_code(p.levels);
+    L.vmask = r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
+    return L;
+}
+
+struct Timer {
+    bool on;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    Timer(bool o, cudaStream_t s) : on(o), st(s) {}
+    int mark() {
+        if (!on) return -1;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        return (int)ev.size() - 1;
+    }
+    float ms(int a, int b) {
+        if (!on || a < 0 || b < 0) return 0.f;
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+    ~Timer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params &p,
+               cudaStream_t st, burr_handle *h) {
+    const uint32_t vb = value_bytes(r);
+    keep_pool_memory();
+    Arena ar(st);
+    Timer tm((p.flags & BURR_FLAG_TIMING) != 0, st);
+    const int t_begin = tm.mark();
+
+    // inputs on the device
+    const uint64_t *dkeys = keys;
+    const void *dvals = values;
+    if (!is_device_ptr(keys)) {
+        void *d;
+        CK(ar.alloc(&d, n * 8), "alloc keys");
+        CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy keys");
+        dkeys = (const uint64_t *)d;
+    }
+    if (!is_device_ptr(values)) {
+        void *d;
+        CK(ar.alloc(&d, n * vb), "alloc values");
+        CK(cudaMemcpyAsync(d, values, n * vb, cudaMemcpyHostToDevice, st), "copy values");
+        dvals = d;
+    }
+
+    // scratch sized for layer 0 (later layers and a normal base case are smaller)
+    const uint64_t m0 = layer_slots(n, p.load_factor);
+    uint64_t cap_m = std::max<uint64_t>(m0, 64), cap_nb = num_buckets(cap_m, p.bucket_slots);
+    void *sk, *sv, *bst, *ss, *cg, *yg, *bk[2], *bv[2], *ctr;
+    CK(ar.alloc(&sk, n * 8), "alloc sorted keys");
+    CK(ar.alloc(&sv, n * vb), "alloc sorted values");
+    CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
+    CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
+    CK(ar.alloc(&cg, cap_m * 8), "alloc band");
+    CK(ar.alloc(&yg, cap_m * vb), "alloc band values");
+    CK(ar.alloc(&bk[0], n * 8), "alloc bumped keys");
+    CK(ar.alloc(&bv[0], n * vb), "alloc bumped values");
+    bk[1] = bv[1] = nullptr;
+    CK(ar.alloc(&ctr, 64), "alloc counters");
+    unsigned long long *bcount = (unsigned long long *)ctr;
+    uint32_t *err = (uint32_t *)((char *)ctr + 8);
+
+    const uint64_t *cur_k = dkeys;
+    const void *cur_v = dvals;
+    uint64_t cur_n = n;
+    int which = 0;
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        LayerStore &S = h->L[l];
+        S.n = cur_n;
+        S.seed_index = l;
+        if (cur_n == 0) continue;
+        S.m = layer_slots(cur_n, p.load_factor);
+        if (S.m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "layer %u needs %llu slots (>= 2^32)", l,
+                                             (unsigned long long)S.m);
+        S.nb = num_buckets(S.m, p.bucket_slots);
+        S.K = num_partitions(S.m, p.partition_slots, p.min_partition_slots);
+        S.sigma = layer_seed(p.seed, l);
+        const uint64_t tw = (S.nb + 31) / 32;
+        CK(cudaMallocAsync((void **)&S.thresh, tw * 8, st), "alloc thresholds");
+        CK(cudaMallocAsync((void **)&S.z, (S.m / 64) * r * 8, st), "alloc table");
+        CK(cudaMemsetAsync(S.thresh, 0, tw * 8, st), "clear thresholds");
+        if (!bk[which]) {
+            CK(ar.alloc(&bk[which], cur_n * 8), "alloc bumped keys");
+            CK(ar.alloc(&bv[which], cur_n * vb), "alloc bumped values");
+        }
+        CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
+        const LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false);
+        const int t0 = tm.mark();
+        CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+        const int t1 = tm.mark();
+        CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, S.thresh,
+                       (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
+        const int t2 = tm.mark();
+        CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, S.z, st), "backsub");
+        h->launches += kSortKernels + 2;
+        const int t3 = tm.mark();
+        unsigned long long hc[2] = {0, 0};
+        CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
+        CK(cudaStreamSynchronize(st), "layer");
+        const uint32_t e = (uint32_t)(hc[1] & 0xffffffffu);
+        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the 512-slot window", l);
+        if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
+        S.nbumped = hc[0];
+        h->stage_ms[l][0] = tm.ms(t0, t1);
+        h->stage_ms[l][1] = tm.ms(t1, t2);
+        h->stage_ms[l][2] = tm.ms(t2, t3);
+        cur_k = (const uint64_t *)bk[which];
+        cur_v = bv[which];
+        cur_n = S.nbumped;
+        which ^= 1;   // layer l+1 reads this list and bumps into the other one (n_{l+1} <= n_l)
+    }
+
+    // base case: no bumping; grow by 10% and change the seed until it solves
+    LayerStore &F = h->L[p.layers];
+    F.n = cur_n;
+    if (cur_n > 0) {
+        bool solved = false;
+        for (uint32_t a = 0; a <= p.fallback_max_retries && !solved; ++a) {
+            if (F.z) {
+                cudaFreeAsync(F.z, st);
+                F.z = nullptr;
+            }
+            F.m = fallback_slots(cur_n, p.fallback_slack, a);
+            if (F.m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "base case needs >= 2^32 slots");
+            F.nb = num_buckets(F.m, p.bucket_slots);
+            F.K = 1;
+            F.seed_index = p.layers + a;
+            F.sigma = layer_seed(p.seed, F.seed_index);
+            if (F.m > cap_m) {
+                ar.release(cg);
+                ar.release(yg);
+                ar.release(bst);
+                ar.release(ss);
+                cap_m = F.m;
+                cap_nb = num_buckets(cap_m, p.bucket_slots);
+                CK(ar.alloc(&cg, cap_m * 8), "alloc band");
+                CK(ar.alloc(&yg, cap_m * vb), "alloc band values");
+                CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
+                CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
+            }
+            CK(cudaMallocAsync((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");
+            CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
+            const LayerDesc L = make_desc(p, r, cur_n, F.m, F.sigma, 1, true);
+            const int t0 = tm.mark();
+            CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+            const int t1 = tm.mark();
+            CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr,
+                           nullptr, nullptr, bcount, err, st), "band");
+            h->launches += kSortKernels + 1;
+            uint32_t he = 0;
+            CK(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
+            CK(cudaStreamSynchronize(st), "base case");
+            if (he & ~kErrUnsolvable) return fail(BURR_ERR_INTERNAL, "base case: device error 0x%x", he);
+            if (he & kErrUnsolvable) continue;
+            const int t2 = tm.mark();
+            CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, F.z, st), "backsub");
+            h->launches += 1;
+            const int t3 = tm.mark();
+            solved = true;
+            h->fb_attempt = a;
+            h->stage_ms[p.layers][0] = tm.ms(t0, t1);
+            h->stage_ms[p.layers][1] = tm.ms(t1, t2);
+            h->stage_ms[p.layers][2] = tm.ms(t2, t3);
+        }
+        if (!solved)
+            return fail(BURR_ERR_UNSOLVABLE, "base case unsolved after %u retries (duplicate keys?)",
+                        p.fallback_max_retries);
+    }
+    const int t_end = tm.mark();
+    CK(cudaStreamSynchronize(st), "build");
+    h->total_ms = tm.ms(t_begin, t_end);
+    return BURR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int burr_default_params(burr_params *p) {
+    if (!p) return fail(BURR_ERR_INVALID, "params pointer is NULL");
+    memset(p, 0, sizeof(*p));
+    p->ribbon_width = 64;
+    p->bucket_slots = 128;
+    p->threshold_mode = BURR_THRESH_2BIT;
+    p->layers = 4;
+    p->levels[0] = 0;
+    p->levels[1] = 32;
+    p->levels[2] = 64;
+    p->levels[3] = 128;
+    p->load_factor = 1.015;
+    p->partition_slots = 65536;
+    p->min_partition_slots = 65536;
+    p->seed = 0x5EED5EED5EED5EEDull;
+    p->fallback_slack = 0.1;
+    p->fallback_max_retries = 16;
+    p->flags = 0;
+    return BURR_OK;
+}
+
+int burr_build(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *pin,
+               void *stream, burr_handle **out) {
+    if (!out) return fail(BURR_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    burr_params p;
+    if (pin) p = *pin;
+    else burr_default_params(&p);
+    int rc = validate(p, r);
+    if (rc) return rc;
+    if (n > 0 && (!keys || !values)) return fail(BURR_ERR_INVALID, "keys/values are NULL");
+    if (n >= (1ull << 32)) return fail(BURR_ERR_INVALID, "n >= 2^32");
+    burr_handle *h = new (std::nothrow) burr_handle();
+    if (!h) return fail(BURR_ERR_OOM, "host allocation");
+    h->p = p;
+    h->r = r;
+    h->vbytes = value_bytes(r);
+    h->n = n;
+    for (uint32_t l = 0; l <= p.layers; ++l) h->L[l].seed_index = l;
+    if (n > 0) {
+        rc = build_impl(keys, values, n, r, p, (cudaStream_t)stream, h);
+        if (rc) {
+            cudaStreamSynchronize((cudaStream_t)stream);
+            free_layers(h);
+            delete h;
+            return rc;
+        }
+    }
+    *out = h;
+    return BURR_OK;
+}
+
+int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n, void *stream) {
+    if (!h) return fail(BURR_ERR_INVALID, "handle is NULL");
+    if (n == 0) return BURR_OK;
+    if (!keys || !out) return fail(BURR_ERR_INVALID, "keys/out are NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    QueryDesc Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.r = h->r;
+    Q.B = h->p.bucket_slots;
+    Q.layers = h->p.layers;
+    for (int i = 0; i < 4; ++i) Q.levels[i] = h->p.levels[i];
+    for (uint32_t l = 0; l <= h->p.layers; ++l) {
+        Q.m[l] = h->L[l].m;
+        Q.sigma[l] = layer_seed(h->p.seed, h->L[l].seed_index);
+        if (l < h->p.layers) Q.thresh[l] = h->L[l].thresh;
+        Q.z[l] = h->L[l].z;
+    }
+    const uint32_t vb = h->vbytes;
+    const bool dk = is_device_ptr(keys), dout = is_device_ptr(out);
+    if (dk && dout) {
+        CK(launch_query(Q, vb, keys, out, n, st), "query");
+        return BURR_OK;
+    }
+    keep_pool_memory();
+    Arena ar(st);
+    const uint64_t *k = keys;
+    void *o = out;
+    if (!dk) {
+        void *d;
+        CK(ar.alloc(&d, n * 8), "alloc query keys");
+        CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy query keys");
+        k = (const uint64_t *)d;
+    }
+    if (!dout) CK(ar.alloc(&o, n * vb), "alloc query output");
+    CK(launch_query(Q, vb, k, o, n, st), "query");
+    if (!dout) CK(cudaMemcpyAsync(out, o, n * vb, cudaMemcpyDeviceToHost, st), "copy query output");
+    CK(cudaStreamSynchronize(st), "query");
+    return BURR_OK;
+}
+
+int burr_size_bytes(const burr_handle *h, uint64_t *bytes) {
+    if (!h || !bytes) return fail(BURR_ERR_INVALID, "NULL argument");
+    uint64_t b = 64;
+    for (uint32_t l = 0; l <= h->p.layers; ++l) {
+        const LayerStore &S = h->L[l];
+        if (l < h->p.layers) b += 8 * ((S.nb + 31) / 32);
+        b += 8 * (S.m / 64) * h->r;
+    }
+    *bytes = b;
+    return BURR_OK;
+}
+
+static uint8_t *put32(uint8_t *q, uint32_t v) {
+    memcpy(q, &v, 4);
+    return q + 4;
+}
+static uint8_t *put64(uint8_t *q, uint64_t v) {
+    memcpy(q, &v, 8);
+    return q + 8;
+}
+
+int burr_export(const burr_handle *h, void *host_buf, uint64_t *len) {
+    if (!h || !len) return fail(BURR_ERR_INVALID, "NULL argument");
+    const burr_params &p = h->p;
+    const uint32_t r = h->r;
+    uint64_t need = 4 * 10 + 8 * 4 + (uint64_t)p.layers * 8 * 5 + 8 * 4;
+    for (uint32_t l = 0; l < p.layers; ++l) need += 8 * ((h->L[l].nb + 31) / 32) + 8 * (h->L[l].m / 64) * r;
+    need += 8 * (h->L[p.layers].m / 64) * r;
+    if (!host_buf || *len < need) {
+        *len = need;
+        return fail(BURR_ERR_INVALID, "export buffer too small (%llu bytes needed)", (unsigned long long)need);
+    }
+    uint8_t *q = (uint8_t *)host_buf;
+    q = put32(q, 0x52525542u);
+    q = put32(q, 1);
+    q = put32(q, r);
+    q = put32(q, p.ribbon_width);
+    q = put32(q, p.bucket_slots);
+    q = put32(q, p.layers);
+    for (int i = 0; i < 4; ++i) q = put32(q, p.levels[i]);
+    uint64_t abits;
+    memcpy(&abits, &p.load_factor, 8);
+    q = put64(q, p.seed);
+    q = put64(q, abits);
+    q = put64(q, h->n);
+    q = put64(q, p.partition_slots);
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        const LayerStore &S = h->L[l];
+        q = put64(q, S.n);
+        q = put64(q, S.m);
+        q = put64(q, S.K);
+        q = put64(q, S.nb);
+        q = put64(q, S.nbumped);
+    }
+    const LayerStore &F = h->L[p.layers];
+    q = put64(q, F.n);
+    q = put64(q, F.m);
+    q = put64(q, F.seed_index);
+    q = put64(q, h->fb_attempt);
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        const LayerStore &S = h->L[l];
+        const uint64_t tw = (S.nb + 31) / 32, zw = (S.m / 64) * r;
+        if (tw) CK(cudaMemcpy(q, S.thresh, tw * 8, cudaMemcpyDeviceToHost), "export thresholds");
+        q += tw * 8;
+        if (zw) CK(cudaMemcpy(q, S.z, zw * 8, cudaMemcpyDeviceToHost), "export table");
+        q += zw * 8;
+    }
+    const uint64_t zw = (F.m / 64) * r;
+    if (zw) CK(cudaMemcpy(q, F.z, zw * 8, cudaMemcpyDeviceToHost), "export base case");
+    q += zw * 8;
+    *len = (uint64_t)(q - (uint8_t *)host_buf);
+    return BURR_OK;
+}
+
+int burr_stats(const burr_handle *h, burr_stats_t *st) {
+    if (!h || !st) return fail(BURR_ERR_INVALID, "NULL argument");
+    memset(st, 0, sizeof(*st));
+    st->n = h->n;
+    st->r = h->r;
+    st->layers = h->p.layers;
+    for (uint32_t l = 0; l <= h->p.layers; ++l) {
+        st->layer_n[l] = h->L[l].n;
+        st->layer_m[l] = h->L[l].m;
+        st->layer_parts[l] = h->L[l].K;
+        st->layer_bumped[l] = h->L[l].nbumped;
+        for (int s = 0; s < 3; ++s) st->stage_ms[l][s] = h->stage_ms[l][s];
+    }
+    st->fallback_attempt = h->fb_attempt;
+    st->total_ms = h->total_ms;
+    uint64_t b = 0;
+    burr_size_bytes(h, &b);
+    st->table_bytes = b;
+    st->kernel_launches = h->launches;
+    return BURR_OK;
+}
+
+void burr_free(burr_handle *h) {
+    if (!h) return;
+    free_layers(h);
+    delete h;
+}
+
+const char *burr_strerror(int code) {
+    switch (code) {
+    case BURR_OK: return "ok";
+    case BURR_ERR_INVALID: return "invalid argument";
+    case BURR_ERR_OOM: return "out of device memory";
+    case BURR_ERR_UNSOLVABLE: return "unsolvable (base case retries exhausted)";
+    case BURR_ERR_TIMEOUT: return "device wait timed out";
+    case BURR_ERR_CUDA: return "CUDA error";
+    case BURR_ERR_INTERNAL: return "internal capacity check failed";
+    default: return "unknown error";
+    }
+}
+
+const char *burr_last_error(void) { return g_err.c_str(); }
+
+int burr_stage_hash(const uint64_t *d_keys, uint64_t n, uint64_t seed, uint32_t layer_index, uint64_t m,
+                    uint32_t *d_start, uint64_t *d_coeff, void *stream) {
+    if (m < kW || m % 64 || m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "m must be a multiple of 64 in [64, 2^32)");
+    if (n && (!d_keys || !d_start || !d_coeff)) return fail(BURR_ERR_INVALID, "NULL argument");
+    CK(launch_hash(d_keys, n, layer_seed(seed, layer_index), m - kW + 1, d_start, d_coeff,
+                   (cudaStream_t)stream), "hash");
+    return BURR_OK;
+}
+
+int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, uint32_t r, uint64_t seed,
+                    uint32_t layer_index, uint64_t m, uint64_t *d_sorted_keys, void *d_sorted_values,
+                    uint32_t *d_bucket_start, void *stream) {
+    if (r < 1 || r > 32) return fail(BURR_ERR_INVALID, "r outside [1,32]");
+    if (m < kW || m % 64 || m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "m must be a multiple of 64 in [64, 2^32)");
+    if (n >= (1ull << 32)) return fail(BURR_ERR_INVALID, "n >= 2^32");
+    burr_params p;
+    burr_default_params(&p);
+    cudaStream_t st = (cudaStream_t)stream;
+    const LayerDesc L = make_desc(p, r, n, m, layer_seed(seed, layer_index), 1, false);
+    const uint32_t vb = value_bytes(r);
+    keep_pool_memory();
+    Arena ar(st);
+    void *ss;
+    CK(ar.alloc(&ss, sort_scratch_bytes(n, m, vb)), "alloc sort scratch");
+    CK(launch_sort(L, vb, d_keys, d_values, d_sorted_keys, d_sorted_values, d_bucket_start, ss, nullptr, st),
+       "sort");
+    return BURR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// burr_internal.cuh -- device helpers and launch descriptors shared by the
+// CUDA translation units of libburr.so (never included by the oracle).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "burr.h"
+
+namespace burr {
+
+constexpr uint32_t kW = 64;                       // ribbon width (Sec. 2)
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+// error bits written by kernels into the build's device error word
+constexpr uint32_t kErrRingOverflow = 1u;         // a pivot left the on-chip window
+constexpr uint32_t kErrUnsolvable = 2u;           // base case: an equation was dependent
+constexpr uint32_t kErrBucketSort = 4u;           // a level-2 sort bin exceeded its capacity
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t layer_seed(uint64_t seed, uint64_t index) {
+    return mix64(seed ^ ((index + 1) * kGolden));
+}
+
+// Start slot in [0, range): floor(h * range / 2^64), range = m - w + 1.
+__device__ __forceinline__ uint32_t start_slot(uint64_t key, uint64_t sigma, uint64_t range) {
+    return (uint32_t)__umul64hi(mix64(key ^ sigma), range);
+}
+
+// The equation of a key: start slot and 64-bit coefficient row (bit 0 set).
+__device__ __forceinline__ void equation(uint64_t key, uint64_t sigma, uint64_t range,
+                                         uint32_t &start, uint64_t &coeff) {
+    const uint64_t h = mix64(key ^ sigma);
+    start = (uint32_t)__umul64hi(h, range);
+    coeff = mix64(h + sigma) | 1ull;
+}
+
+// One layer as the kernels see it.
+struct LayerDesc {
+    uint64_t n;          // equations (keys) in the layer
+    uint64_t m;          // slots, multiple of 64, < 2^32
+    uint64_t range;      // start positions m - w + 1
+    uint64_t sigma;      // hash seed of the layer
+    uint64_t nb;         // buckets
+    uint64_t P;          // partition slots
+    uint32_t K;          // partitions
+    uint32_t r;          // value bits
+    uint32_t B;          // bucket slots
+    uint32_t fallback;   // 1: base case (no thresholds, failure = unsolvable)
+    uint32_t levels[4];
+    uint32_t forced_code;
+    uint32_t vmask;      // (1 << r) - 1
+};
+
+// Sorting by bucket: level-1 bins of 2^shift1 start slots, level-2 buckets.
+struct SortPlan {
+    uint32_t shift1;     // log2 start slots per level-1 bin
+    uint32_t nbins1;     // level-1 bins
+};
+
+constexpr uint64_t kSortKernels = 4;   // kernels one launch_sort enqueues (n > 0)
+size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes);
+
+// Sort n (key, value) pairs of a layer into bucket order.
+// scratch: sort_scratch_bytes(n, m, vbytes) bytes of device memory.
+cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                        uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
+                        uint32_t *err, cudaStream_t st);
+
+// Band + bump (or base case), writing the band of every partition to Cg/Yg.
+cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                        const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh,
+                        uint64_t *bumped_keys, void *bumped_vals, unsigned long long *bumped_count,
+                        uint32_t *err, cudaStream_t st);
+
+// Back-substitution of every partition: Z from the band.
+cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
+                           uint64_t *Z, cudaStream_t st);
+
+// Query descriptor: every layer of a handle.
+struct QueryDesc {
+    uint32_t r;
+    uint32_t B;
+    uint32_t layers;          // bumping layers
+    uint32_t levels[4];
+    uint64_t m[BURR_MAX_LAYERS + 1];
+    uint64_t sigma[BURR_MAX_LAYERS + 1];
+    const uint64_t *thresh[BURR_MAX_LAYERS];
+    const uint64_t *z[BURR_MAX_LAYERS + 1];   // [layers] = base case
+};
+
+cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *keys, void *out,
+                         uint64_t n, cudaStream_t st);
+
+cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t range,
+                        uint32_t *start, uint64_t *coeff, cudaStream_t st);
+
+inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap) {
+    uint64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+}  // namespace burr

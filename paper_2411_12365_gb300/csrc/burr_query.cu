@@ -1,0 +1,94 @@
+// burr_query.cu -- the layered query (Sec. 2: AND the key's coefficients with
+// the table window, parity per value bit; a key below its bucket's threshold
+// was bumped and is looked up in the next layer) and the standalone hash stage.
+#include "burr_internal.cuh"
+
+namespace burr {
+
+namespace {
+
+constexpr int kQThreads = 256;
+
+// r-bit value of the window [s, s+63] selected by coefficient row c.
+__device__ __forceinline__ uint32_t eval_window(const uint64_t *__restrict__ z, uint32_t r, uint32_t s,
+                                                uint64_t c) {
+    const uint64_t blk = s >> 6;
+    const uint32_t o = s & 63u;
+    const uint64_t *w0 = z + blk * r;
+    uint32_t v = 0;
+    if (o == 0) {
+        for (uint32_t k = 0; k < r; ++k) v |= (uint32_t)(__popcll(__ldg(w0 + k) & c) & 1) << k;
+    } else {
+        const uint64_t *w1 = w0 + r;
+        for (uint32_t k = 0; k < r; ++k) {
+            const uint64_t win = (__ldg(w0 + k) >> o) | (__ldg(w1 + k) << (64 - o));
+            v |= (uint32_t)(__popcll(win & c) & 1) << k;
+        }
+    }
+    return v;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kQThreads)
+k_query(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t log2B = 31 - __clz(Q.B);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = keys[i];
+        uint32_t v = 0;
+        uint32_t l = 0;
+        for (; l < Q.layers; ++l) {
+            const uint64_t m = Q.m[l];
+            if (m == 0) break;
+            const uint64_t h = mix64(key ^ Q.sigma[l]);
+            const uint32_t s = (uint32_t)__umul64hi(h, m - kW + 1);
+            const uint32_t b = s >> log2B;
+            const uint32_t off = s & (Q.B - 1);
+            const uint32_t code = (uint32_t)(__ldg(Q.thresh[l] + (b >> 5)) >> (2 * (b & 31))) & 3u;
+            if (off < Q.levels[code]) continue;               // bumped: next layer
+            v = eval_window(Q.z[l], Q.r, s, mix64(h + Q.sigma[l]) | 1ull);
+            break;
+        }
+        if (l == Q.layers && Q.m[l] != 0) {                    // base case
+            const uint64_t h = mix64(key ^ Q.sigma[l]);
+            const uint32_t s = (uint32_t)__umul64hi(h, Q.m[l] - kW + 1);
+            v = eval_window(Q.z[l], Q.r, s, mix64(h + Q.sigma[l]) | 1ull);
+        }
+        out[i] = (V)v;
+    }
+}
+
+__global__ void k_hash(const uint64_t *__restrict__ keys, uint64_t n, uint64_t sigma, uint64_t range,
+                       uint32_t *__restrict__ start, uint64_t *__restrict__ coeff) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t s;
+        uint64_t c;
+        equation(keys[i], sigma, range, s, c);
+        start[i] = s;
+        coeff[i] = c;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *keys, void *out, uint64_t n,
+                         cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = grid_for(n, kQThreads, 152u * 64u);
+    switch (vbytes) {
+    case 1: k_query<uint8_t><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n); break;
+    case 2: k_query<uint16_t><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n); break;
+    default: k_query<uint32_t><<<grid, kQThreads, 0, st>>>(Q, keys, (uint32_t *)out, n); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t range, uint32_t *start,
+                        uint64_t *coeff, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_hash<<<grid_for(n, 256, 152u * 32u), 256, 0, st>>>(keys, n, sigma, range, start, coeff);
+    return cudaGetLastError();
+}
+
+}  // namespace burr

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/burr.h declares (host-only calls; no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "burr.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(burr_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_12365_gb300 import build as B
+    path = B.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for f in ("burr_build", "burr_query", "burr_free", "burr_export", "burr_default_params"):
+        assert f in fns
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2411_12365_gb300 import burr
+    assert sorted(burr.EXPORTED) == declared_functions()
+
+
+def test_default_params_layout(lib):
+    from paper_2411_12365_gb300 import burr
+    burr.load(os.path.join(ROOT, "paper_2411_12365_gb300", "_lib", "libburr.so"))
+    p = burr.default_params()
+    assert C.sizeof(burr.Params) == 80
+    assert (p.ribbon_width, p.bucket_slots, p.layers, list(p.levels)) == (64, 128, 4, [0, 32, 64, 128])
+    assert p.load_factor == 1.015 and p.partition_slots == 65536 and p.fallback_max_retries == 16
+    # the oracle's defaults are the same workload
+    from oracle import oracle as O
+    q = O.default_params()
+    assert (q.alpha, q.partition_slots, q.min_partition_slots, q.seed, q.layers, q.fb_slack) == \
+        (p.load_factor, p.partition_slots, p.min_partition_slots, p.seed, p.layers, p.fallback_slack)
+
+
+def test_strerror(lib):
+    lib.burr_strerror.restype = C.c_char_p
+    assert lib.burr_strerror(-3).decode().startswith("unsolvable")

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path through the C ABI against the serial CPU oracle.
+
+Bit-exact everywhere (integer GF(2) work): hash records, bucket grouping,
+whole-structure exports (sizes, thresholds, tables of every layer and the
+base case) and query outputs.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_12365_gb300 import inputs as I
+from tests.export_format import describe_difference, parse
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_12365_gb300 import burr  # noqa: E402
+
+DEV = "cuda"
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _vals_np(t):
+    a = t.cpu().numpy()
+    return a.view({1: np.uint8, 2: np.uint16, 4: np.uint32}[a.dtype.itemsize]).astype(np.uint32)
+
+
+def _kv(n, r, seed=I.KEY_SEED, offset=0):
+    k = I.keys_torch(n, DEV, seed=seed, offset=offset)
+    return k, I.values_torch(k, r)
+
+
+@pytest.mark.parametrize("n,m,layer", [(1_000_003, 1_015_872, 0), (4097, 4160, 3), (1, 64, 7)])
+def test_stage_hash_matches_oracle(n, m, layer):
+    seed = 0xABCDEF
+    keys = I.keys_torch(n, DEV)
+    s, c = burr.stage_hash(keys, seed, layer, m)
+    os_, oc = O.hash_many(_u64(keys), O.layer_seed(seed, layer), m)
+    assert np.array_equal(s.cpu().numpy().view(np.uint32).astype(np.uint64), os_)
+    assert np.array_equal(c.cpu().numpy().view(np.uint64), oc)
+
+
+@pytest.mark.parametrize("n,r", [(300_007, 8), (70_001, 16), (5, 32)])
+def test_stage_sort_groups_by_bucket(n, r):
+    seed, layer = 77, 1
+    keys, vals = _kv(n, r, seed=n)
+    m = O.layer_slots(n, 1.015)
+    sk, sv, bs = burr.stage_sort(keys, vals, r, seed, layer, m)
+    sk, sv, bs = _u64(sk), _vals_np(sv), bs.cpu().numpy().astype(np.int64)
+    nb = (m - 64 + 128) // 128
+    assert bs[0] == 0 and bs[-1] == n and np.all(np.diff(bs) >= 0) and len(bs) == nb + 1
+    starts, _ = O.hash_many(sk, O.layer_seed(seed, layer), m)
+    bucket_of_pos = np.repeat(np.arange(nb), np.diff(bs))
+    assert np.array_equal(starts // 128, bucket_of_pos)
+    # same (key, value) pairs
+    ok, ov = _u64(keys), _vals_np(vals)
+    a = np.lexsort((ov, ok))
+    b = np.lexsort((sv, sk))
+    assert np.array_equal(ok[a], sk[b]) and np.array_equal(ov[a], sv[b])
+
+
+def _check_build(n, r, seed=I.KEY_SEED, **params):
+    keys, vals = _kv(n, r, seed=seed)
+    h = burr.build(keys, vals, r, **params)
+    got = h.export()
+    names = {"load_factor": "alpha", "fallback_max_retries": "fb_max_retries", "fallback_slack": "fb_slack"}
+    ref = O.build(_u64(keys), _vals_np(vals), r=r, **{names.get(k, k): v for k, v in params.items()})
+    assert ref.ok
+    want = ref.export()
+    assert got == want, describe_difference(got, want)
+    if n:
+        assert torch.equal(h.query(keys), vals)
+    return h, ref, keys, vals
+
+
+BUILD_CASES = [
+    (0, 8, {}), (1, 8, {}), (2, 1, {}), (100, 3, {}),
+    (5000, 8, dict(partition_slots=1024, min_partition_slots=1024)),
+    (65573, 8, dict(partition_slots=4096, min_partition_slots=4096)),       # ragged tail
+    (1 << 20, 8, {}),                                                       # 2^20, P = 2^16
+    (200_003, 16, dict(partition_slots=8192, min_partition_slots=8192)),
+    (100_000, 32, dict(partition_slots=2048, min_partition_slots=2048)),
+    (150_001, 1, dict(partition_slots=4096, min_partition_slots=0)),
+    (70_000, 5, dict(partition_slots=384, min_partition_slots=0)),
+    (90_000, 4, dict(partition_slots=128, min_partition_slots=0)),          # a cut at every bucket
+]
+
+
+@pytest.mark.parametrize("n,r,params", BUILD_CASES)
+def test_build_matches_oracle(n, r, params):
+    _check_build(n, r, **params)
+
+
+@pytest.mark.parametrize("alpha,P", [(1.3, 256), (1.6, 4096), (2.2, 1024), (0.8, 65536)])
+def test_overloaded_layers_match_oracle(alpha, P):
+    h, ref, *_ = _check_build(60_000, 8, load_factor=alpha, partition_slots=P, min_partition_slots=0)
+    if alpha >= 1.6:
+        codes = set()
+        for L in parse(h.export())["layers"]:
+            for wd in L["thresh"]:
+                codes |= {(int(wd) >> (2 * i)) & 3 for i in range(32)}
+        assert codes == {0, 1, 2, 3}
+
+
+@pytest.mark.parametrize("layers", [0, 1, 2, 8])
+def test_layer_count_and_base_case(layers):
+    _check_build(30_000, 8, layers=layers, partition_slots=2048, min_partition_slots=2048)
+
+
+def test_negative_queries_match_oracle():
+    h, ref, keys, vals = _check_build(1 << 18, 8, partition_slots=8192, min_partition_slots=8192)
+    neg = I.keys_torch(1 << 18, DEV, offset=1 << 18)
+    assert np.array_equal(_vals_np(h.query(neg)), ref.query(_u64(neg)))
+
+
+def test_host_pointers():
+    n, r = 50_000, 16
+    keys, vals = _kv(n, r)
+    hd = burr.build(keys, vals, r, partition_slots=4096)
+    hh = burr.build(_u64(keys), vals.cpu().numpy().view(np.uint16), r, partition_slots=4096)
+    assert hd.export() == hh.export()
+    out = hh.query(_u64(keys))
+    assert isinstance(out, np.ndarray) and np.array_equal(out.astype(np.uint32), _vals_np(vals))
+
+
+def test_determinism():
+    keys, vals = _kv(300_000, 8)
+    a = burr.build(keys, vals, 8).export()
+    b = burr.build(keys, vals, 8).export()
+    assert a == b
+
+
+def test_duplicate_keys_are_unsolvable():
+    keys, vals = _kv(10_000, 8)
+    keys[5] = keys[9]
+    vals[5] = vals[9]
+    with pytest.raises(burr.BurrError) as e:
+        burr.build(keys, vals, 8, fallback_max_retries=2)
+    assert e.value.code == burr.ERR_UNSOLVABLE
+
+
+@pytest.mark.parametrize("bad", [dict(ribbon_width=32), dict(bucket_slots=96), dict(partition_slots=100),
+                                 dict(levels=(0, 32, 64, 100)), dict(load_factor=0.0), dict(layers=9)])
+def test_invalid_params(bad):
+    keys, vals = _kv(100, 8)
+    with pytest.raises(burr.BurrError) as e:
+        burr.build(keys, vals, 8, **bad)
+    assert e.value.code == burr.ERR_INVALID
+
+
+def test_invalid_r():
+    keys, vals = _kv(100, 8)
+    for r in (0, 33):
+        with pytest.raises(burr.BurrError):
+            burr.build(keys, vals, r)
+
+
+def _owned(j, K, P, m):
+    return (0 if j == 0 else j * P + 64), (m if j == K - 1 else (j + 1) * P + 64)
+
+
+def test_full_size_1e8_sampled_partitions_and_invariants():
+    """n = 10^8, r = 8, P = 2^16 (the benchmark's launch configuration)."""
+    n, r, P = 100_000_000, 8, 65536
+    keys, vals = _kv(n, r)
+    h = burr.build(keys, vals, r, partition_slots=P, min_partition_slots=P)
+    st = h.stats()
+    # query(x) = f(x) for every key
+    assert torch.equal(h.query(keys), vals)
+    # negatives: fingerprint matches with probability 2^-r
+    neg = I.keys_torch(1 << 22, DEV, offset=n)
+    hits = int((h.query(neg) == I.values_torch(neg, r)).sum())
+    mean = (1 << 22) / 256.0
+    assert abs(hits - mean) < 6 * (mean ** 0.5)
+    # layer sizes follow the sizing rule
+    for l in range(4):
+        assert st["layer_m"][l] == O.layer_slots(st["layer_n"][l], 1.015)
+        if l < 3:
+            assert st["layer_n"][l + 1] == st["layer_bumped"][l]
+    # sampled layer-0 partitions rebuilt alone by the oracle (partitions are independent)
+    ex = parse(h.export())
+    L0 = ex["layers"][0]
+    m, K = L0["m"], L0["parts"]
+    assert K == O.num_partitions(m, P, P)
+    k_np = _u64(keys)
+    v_np = _vals_np(vals)
+    sigma = O.layer_seed(0x5EED5EED5EED5EED, 0)
+    starts, _ = O.hash_many(k_np, sigma, m)
+    cuts = [j * P for j in range(1, K)]
+    for j in (0, 1, K // 2, K - 1):
+        lo, hi = j * P, (m - 63 if j == K - 1 else (j + 1) * P)
+        sel = (starts >= lo) & (starts < hi)
+        res = O.build_layer(k_np[sel], v_np[sel], r, m, sigma, cuts=cuts)
+        a, b = _owned(j, K, P, m)
+        assert np.array_equal(res.z[(a // 64) * r:(b // 64) * r], L0["z"][(a // 64) * r:(b // 64) * r])
+        b0, b1 = lo // 128, (hi + 127) // 128
+        tw = lambda t, b: (int(t[b // 32]) >> (2 * (b % 32))) & 3  # noqa: E731
+        assert [tw(res.thresh, b) for b in range(b0, b1)] == [tw(L0["thresh"], b) for b in range(b0, b1)]
