@@ -52,7 +52,7 @@ class Stats(C.Structure):
 
 EXPORTED = ["burr_default_params", "burr_build", "burr_query", "burr_size_bytes", "burr_export",
             "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
-            "burr_stage_sort"]
+            "burr_stage_sort", "burr_stage_sort_noalloc"]
 
 
 def lib_path() -> str:
@@ -92,6 +92,8 @@ def load(path: str | None = None):
         L.burr_stage_hash.restype = i
         L.burr_stage_sort.argtypes = [p, p, u64, u32, u64, u32, u64, p, p, p, p]
         L.burr_stage_sort.restype = i
+        L.burr_stage_sort_noalloc.argtypes = [p, p, u64, u32, u64, u32, u64, p, p, p, p]
+        L.burr_stage_sort_noalloc.restype = i
         _lib = L
         return L
 

@@ -145,6 +145,11 @@ struct LayerStore {
 
 }  // namespace
 
+int burr::set_error(int code, const char *msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+
 struct burr_handle {
     burr_params p;
     uint32_t r = 0, vbytes = 0;

@@ -101,6 +101,9 @@ cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *ke
 cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t range,
                         uint32_t *start, uint64_t *coeff, cudaStream_t st);
 
+// Record a message for burr_last_error() and return `code`.
+int set_error(int code, const char *msg);
+
 inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap) {
     uint64_t g = (work + per_block - 1) / per_block;
     if (g < 1) g = 1;
