@@ -65,7 +65,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or _build.LIB
+        path = path or os.environ.get("BURR_LIB") or _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libburr.so not built ({path}); run __graft_entry__.build()")
         L = C.CDLL(path)

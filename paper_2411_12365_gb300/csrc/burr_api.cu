@@ -196,11 +196,12 @@ struct Timer {
     cudaStream_t st;
     std::vector<cudaEvent_t> ev;
     Timer(bool o, cudaStream_t s) : on(o), st(s) {}
-    int mark() {
+    int mark() { return mark_on(st); }
+    int mark_on(cudaStream_t s) {
         if (!on) return -1;
         cudaEvent_t e;
         cudaEventCreate(&e);
-        cudaEventRecord(e, st);
+        cudaEventRecord(e, s);
         ev.push_back(e);
         return (int)ev.size() - 1;
     }
@@ -215,13 +216,52 @@ struct Timer {
     }
 };
 
+// A second stream for back-substitution: layer l's back-substitution does not
+// feed layer l+1 (only its bumped keys do), so it runs while layer l+1 sorts
+// and bands.  The band buffers alternate between two sets so that layer l+1
+// never overwrites the band layer l is still solving.  On destruction the
+// build stream waits for the side stream, so every later free on the build
+// stream is ordered after the side stream's reads.
+struct SideStream {
+    cudaStream_t main, side = nullptr;
+    cudaEvent_t ev[4] = {};
+    explicit SideStream(cudaStream_t m) : main(m) {}
+    cudaError_t init() {
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        return e;
+    }
+    // `to` waits for everything enqueued so far on `from`
+    cudaError_t order(cudaStream_t from, cudaStream_t to, int slot) {
+        cudaError_t e = cudaEventRecord(ev[slot], from);
+        return e == cudaSuccess ? cudaStreamWaitEvent(to, ev[slot], 0) : e;
+    }
+    // mark the end of the back-substitution that read band set `set`
+    cudaError_t solved(int set) { return cudaEventRecord(ev[set], side); }
+    // the main stream waits until band set `set` is no longer read (no-op if never used)
+    cudaError_t reuse(int set) { return cudaStreamWaitEvent(main, ev[set], 0); }
+    ~SideStream() {
+        if (side) {
+            if (ev[3] && cudaEventRecord(ev[3], side) == cudaSuccess) cudaStreamWaitEvent(main, ev[3], 0);
+            cudaStreamDestroy(side);
+        }
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params &p,
                cudaStream_t st, burr_handle *h) {
     const uint32_t vb = value_bytes(r);
     keep_pool_memory();
     Arena ar(st);
     Timer tm((p.flags & BURR_FLAG_TIMING) != 0, st);
+    SideStream side(st);   // declared after the arena: destroyed first
+    CK(side.init(), "side stream");
     const int t_begin = tm.mark();
+    int tev[BURR_MAX_LAYERS + 1][5];
+    for (auto &row : tev)
+        for (int &x : row) x = -1;
 
     // inputs on the device
     const uint64_t *dkeys = keys;
@@ -247,8 +287,13 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     CK(ar.alloc(&sv, n * vb), "alloc sorted values");
     CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
     CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
+    void *cgs[2] = {nullptr, nullptr}, *ygs[2] = {nullptr, nullptr};
+    uint64_t cgcap[2] = {0, 0};
     CK(ar.alloc(&cg, cap_m * 8), "alloc band");
     CK(ar.alloc(&yg, cap_m * vb), "alloc band values");
+    cgs[0] = cg;
+    ygs[0] = yg;
+    cgcap[0] = cap_m;
     CK(ar.alloc(&bk[0], n * 8), "alloc bumped keys");
     CK(ar.alloc(&bv[0], n * vb), "alloc bumped values");
     bk[1] = bv[1] = nullptr;
@@ -281,15 +326,26 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         }
         CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
         const LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false);
-        const int t0 = tm.mark();
+        const int set = (int)(l & 1);
+        if (cgcap[set] < S.m) {           // second band set, sized by the first layer that uses it
+            CK(ar.alloc(&cgs[set], S.m * 8), "alloc band");
+            CK(ar.alloc(&ygs[set], S.m * vb), "alloc band values");
+            cgcap[set] = S.m;
+        }
+        // the band of layer l overwrites the set that layer l-2 solved: wait for it
+        CK(side.reuse(set), "order");
+        tev[l][0] = tm.mark();
         CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
-        const int t1 = tm.mark();
-        CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, S.thresh,
-                       (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
-        const int t2 = tm.mark();
-        CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, S.z, st), "backsub");
+        tev[l][1] = tm.mark();
+        CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
+                       S.thresh, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
+        tev[l][2] = tm.mark();
+        CK(side.order(st, side.side, 2), "order");
+        tev[l][3] = tm.mark_on(side.side);
+        CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side), "backsub");
+        tev[l][4] = tm.mark_on(side.side);
+        CK(side.solved(set), "order");
         h->launches += kSortKernels + 2;
-        const int t3 = tm.mark();
         unsigned long long hc[2] = {0, 0};
         CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
         CK(cudaStreamSynchronize(st), "layer");
@@ -297,9 +353,6 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the 512-slot window", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
         S.nbumped = hc[0];
-        h->stage_ms[l][0] = tm.ms(t0, t1);
-        h->stage_ms[l][1] = tm.ms(t1, t2);
-        h->stage_ms[l][2] = tm.ms(t2, t3);
         cur_k = (const uint64_t *)bk[which];
         cur_v = bv[which];
         cur_n = S.nbumped;
@@ -322,26 +375,29 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             F.K = 1;
             F.seed_index = p.layers + a;
             F.sigma = layer_seed(p.seed, F.seed_index);
+            const int set = (int)(p.layers & 1);
+            if (cgcap[set] < F.m) {
+                CK(ar.alloc(&cgs[set], F.m * 8), "alloc band");
+                CK(ar.alloc(&ygs[set], F.m * vb), "alloc band values");
+                cgcap[set] = F.m;
+            }
             if (F.m > cap_m) {
-                ar.release(cg);
-                ar.release(yg);
                 ar.release(bst);
                 ar.release(ss);
                 cap_m = F.m;
                 cap_nb = num_buckets(cap_m, p.bucket_slots);
-                CK(ar.alloc(&cg, cap_m * 8), "alloc band");
-                CK(ar.alloc(&yg, cap_m * vb), "alloc band values");
                 CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
                 CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
             }
+            CK(side.reuse(set), "order");
             CK(cudaMallocAsync((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");
             CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
             const LayerDesc L = make_desc(p, r, cur_n, F.m, F.sigma, 1, true);
             const int t0 = tm.mark();
             CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
             const int t1 = tm.mark();
-            CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr,
-                           nullptr, nullptr, bcount, err, st), "band");
+            CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
+                           nullptr, nullptr, nullptr, bcount, err, st), "band");
             h->launches += kSortKernels + 1;
             uint32_t he = 0;
             CK(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
@@ -349,21 +405,31 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             if (he & ~kErrUnsolvable) return fail(BURR_ERR_INTERNAL, "base case: device error 0x%x", he);
             if (he & kErrUnsolvable) continue;
             const int t2 = tm.mark();
-            CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, F.z, st), "backsub");
+            CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], F.z, st), "backsub");
             h->launches += 1;
             const int t3 = tm.mark();
             solved = true;
             h->fb_attempt = a;
-            h->stage_ms[p.layers][0] = tm.ms(t0, t1);
-            h->stage_ms[p.layers][1] = tm.ms(t1, t2);
-            h->stage_ms[p.layers][2] = tm.ms(t2, t3);
+            tev[p.layers][0] = t0;
+            tev[p.layers][1] = t1;
+            tev[p.layers][2] = t2;
+            tev[p.layers][3] = t3;
         }
         if (!solved)
             return fail(BURR_ERR_UNSOLVABLE, "base case unsolved after %u retries (duplicate keys?)",
                         p.fallback_max_retries);
     }
+    CK(side.order(side.side, st, 3), "order");
     const int t_end = tm.mark();
     CK(cudaStreamSynchronize(st), "build");
+    for (uint32_t l = 0; l <= p.layers; ++l) {
+        if (tev[l][0] < 0) continue;
+        h->stage_ms[l][0] = tm.ms(tev[l][0], tev[l][1]);
+        h->stage_ms[l][1] = tm.ms(tev[l][1], tev[l][2]);
+        // back-substitution of a bumping layer runs on the side stream,
+        // overlapped with the next layers; this is its span on that stream
+        h->stage_ms[l][2] = l < p.layers ? tm.ms(tev[l][3], tev[l][4]) : tm.ms(tev[l][2], tev[l][3]);
+    }
     h->total_ms = tm.ms(t_begin, t_end);
     return BURR_OK;
 }

@@ -4,25 +4,31 @@
 //
 // One warp per partition.  The paper gives one partition to one CPU thread,
 // which eliminates the rows one by one.  Here the 32 lanes of a warp insert a
-// whole bucket at once:
+// bucket together:
 //
 //   * The kept set of a bucket does not depend on the order of its rows
 //     inside a threshold band: the threshold is the smallest level t such
 //     that the rows kept so far plus the bucket's rows with offset >= t are
 //     linearly independent, and independence is a property of the set.  The
 //     table does not depend on it either (unique solution with free slots 0).
-//   * So the warp first tries the whole bucket as one set.  Most buckets
+//   * So the warp first inserts the whole bucket as one set.  Most buckets
 //     insert without a dependency.  If the set is dependent it is rolled back
 //     and the bands [l2,l3), [l1,l2), [l0,l1) are inserted from the top until
 //     one is dependent, which fixes the threshold exactly as the row-by-row
 //     elimination in descending offset order would.
-//   * A set is inserted in rounds.  Every pending row is reduced against the
-//     rows stored so far (read-only) until its leading coefficient sits on an
-//     empty slot or the row vanishes (dependent).  Rows that landed on
-//     distinct empty slots are then stored together (equivalent to inserting
-//     them one after the other, because each one's elimination never touched
-//     another's landing slot); rows that landed on an already claimed slot
-//     continue in the next round.
+//   * A set is inserted as a stream.  Each lane takes the next row of the set
+//     (a shared-memory counter) and eliminates it on its own, with no
+//     per-step vote or barrier: one step is one 128-bit compare-and-swap on
+//     the ring slot of the row's leading bit, which either claims the slot if
+//     it is empty (row and right-hand side stored in one atomic write) or
+//     returns the stored row and right-hand side to XOR with.  This is a
+//     sequential insertion in claim order: every slot a row eliminated
+//     against was occupied when read and stays so, and a row is stored only
+//     on a slot that was still empty.
+//   * Rows are staged per bucket in shared memory in ascending offset order
+//     (a counting sort on the 7-bit offset), so each threshold band is a
+//     contiguous range and rows that run through the dense overflow of the
+//     previous buckets start first.
 //   * The live part of the band, [bucket start, bucket start + 512), sits in a
 //     shared-memory ring per warp; slots left behind are final and are
 //     written to the global band in coalesced runs.
@@ -34,16 +40,28 @@ namespace {
 
 constexpr int kRing = 512;
 constexpr uint32_t kRingMask = kRing - 1;
-constexpr int kRPL = 6;                 // rows per lane in one chunk
-constexpr uint32_t kChunk = 32 * kRPL;  // rows inserted per round set
+constexpr int kStage = 256;             // rows of a bucket staged at once
+constexpr int kStagePerLane = kStage / 32;
 constexpr int kBandWarps = 4;           // partitions per CTA
 constexpr unsigned kFull = 0xffffffffu;
 
+constexpr unsigned long long kYValid = 1ull << 32;   // marks a stored right-hand side
+
+struct alignas(16) RingSlot {
+    unsigned long long c;   // stored coefficient row (bit 0 = pivot), 0 = empty
+    unsigned long long y;   // kYValid | right-hand side (low r bits); 0 = empty
+};
+
 struct BandWarpSmem {
-    uint64_t C[kRing];       // stored coefficient rows (bit 0 = pivot), 0 = empty
-    uint32_t Y[kRing];       // stored right-hand sides
-    uint16_t claim[kRing];   // landing-slot claims of one round
-    uint16_t clist[kRing];   // ring indices stored in the current set (rollback)
+    RingSlot ring[kRing];          // live band window
+    uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
+    unsigned long long rc[kStage]; // staged coefficient rows, ascending offset
+    uint32_t ry[kStage];           // staged right-hand sides
+    uint8_t ro[kStage];            // staged offsets
+    uint32_t first[132];           // first staged index of each offset (+ [128] = count)
+    uint32_t next;                 // next staged row to hand out
+    uint32_t ncommit;              // entries of clist
+    uint32_t flag;                 // 1 = dependent set, 2 = ring overflow
 };
 
 template <typename V>
@@ -67,115 +85,163 @@ __device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int 
     __syncwarp();
     for (uint32_t i = lane; i < ncommit; i += 32) {
         const uint32_t ri = S.clist[i];
-        S.C[ri] = 0;
-        S.Y[ri] = 0;
+        S.ring[ri].c = 0;
+        S.ring[ri].y = 0;
     }
     __syncwarp();
 }
 
-// Insert rows [rs, re) of the bucket starting at slot bB whose offset lies in
-// [lo, hi), as one set.  On a dependency (or a ring overflow) every row this
-// call stored is removed again.
+// Stage rows [base, base+cnt) (cnt <= kStage) of the bucket starting at slot
+// bB: equations in ascending offset order; S.first[o] = first index with
+// offset >= o.
 template <typename V>
-__device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, uint32_t rs, uint32_t re,
-                          uint32_t bB, uint32_t lo, uint32_t hi, int lane) {
+__device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, uint32_t base, uint32_t cnt, uint32_t bB,
+                           int lane) {
     const LayerDesc &L = a.L;
-    uint32_t ncommit = 0;
-    for (uint32_t base = rs; base < re; base += kChunk) {
-        uint64_t cur[kRPL];
-        uint32_t pos[kRPL], y[kRPL];
-        uint32_t act = 0;
+    for (int i = lane; i < 132; i += 32) S.first[i] = 0;
+    __syncwarp();
+    uint64_t c[kStagePerLane];
+    uint32_t y[kStagePerLane], o[kStagePerLane], rank[kStagePerLane];
 #pragma unroll
-        for (int k = 0; k < kRPL; ++k) {
-            const uint32_t idx = base + (uint32_t)k * 32u + (uint32_t)lane;
-            cur[k] = 0;
-            pos[k] = 0;
-            y[k] = 0;
-            if (idx < re) {
-                uint32_t s;
-                uint64_t c;
-                equation(a.keys[idx], L.sigma, L.range, s, c);
-                const uint32_t off = s - bB;
-                if (off >= lo && off < hi) {
-                    cur[k] = c;
-                    pos[k] = s;
-                    y[k] = (uint32_t)a.vals[idx] & L.vmask;
-                    act |= 1u << k;
-                }
-            }
+    for (int j = 0; j < kStagePerLane; ++j) {
+        const uint32_t i = (uint32_t)lane + 32u * j;
+        if (i < cnt) {
+            uint32_t s;
+            equation(a.keys[base + i], L.sigma, L.range, s, c[j]);
+            o[j] = s - bB;
+            y[j] = (uint32_t)a.vals[base + i] & L.vmask;
+            rank[j] = atomicAdd(&S.first[o[j]], 1u);
         }
-        while (__any_sync(kFull, act)) {
-            bool fail = false, ovf = false;
-            uint32_t chase = act;
-            while (chase) {
+    }
+    __syncwarp();
+    // exclusive scan of the 128 offset counts, 4 per lane
+    uint32_t v0 = S.first[4 * lane], v1 = S.first[4 * lane + 1], v2 = S.first[4 * lane + 2],
+             v3 = S.first[4 * lane + 3];
+    const uint32_t loc = v0 + v1 + v2 + v3;
+    uint32_t incl = loc;
 #pragma unroll
-                for (int k = 0; k < kRPL; ++k) {
-                    if (chase & (1u << k)) {
-                        const uint32_t ri = pos[k] & kRingMask;
-                        const uint64_t c = S.C[ri];
-                        if (c == 0) {
-                            chase &= ~(1u << k);           // leading bit on an empty slot
-                        } else {
-                            cur[k] ^= c;
-                            y[k] ^= S.Y[ri];
-                            if (cur[k] == 0) {
-                                fail = true;               // the row vanished: dependent set
-                                chase &= ~(1u << k);
-                            } else {
-                                const int tz = __ffsll((long long)cur[k]) - 1;
-                                pos[k] += (uint32_t)tz;
-                                cur[k] >>= tz;
-                                if (pos[k] - bB >= (uint32_t)kRing) {
-                                    ovf = true;
-                                    chase &= ~(1u << k);
-                                }
-                            }
-                        }
-                    }
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += t;
+    }
+    __syncwarp();
+    uint32_t run = incl - loc;
+    S.first[4 * lane] = run;
+    run += v0;
+    S.first[4 * lane + 1] = run;
+    run += v1;
+    S.first[4 * lane + 2] = run;
+    run += v2;
+    S.first[4 * lane + 3] = run;
+    if (lane == 31) S.first[128] = incl;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kStagePerLane; ++j) {
+        const uint32_t i = (uint32_t)lane + 32u * j;
+        if (i < cnt) {
+            const uint32_t p = S.first[o[j]] + rank[j];
+            S.rc[p] = c[j];
+            S.ry[p] = y[j];
+            S.ro[p] = (uint8_t)o[j];
+        }
+    }
+    __syncwarp();
+}
+
+// 128-bit compare-and-swap on a ring slot: if the slot is (0, 0) it becomes
+// (c, y); the previous contents are returned either way.
+__device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, unsigned long long y,
+                                         unsigned long long &oc, unsigned long long &oy) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
+    const unsigned long long zero = 0ull;
+    asm volatile("{\n\t.reg .b128 d, b, v;\n\t"
+                 "mov.b128 b, {%2, %2};\n\t"
+                 "mov.b128 v, {%3, %4};\n\t"
+                 "atom.shared.cas.b128 d, [%5], b, v;\n\t"
+                 "mov.b128 {%0, %1}, d;\n\t}"
+                 : "=l"(oc), "=l"(oy)
+                 : "l"(zero), "l"(c), "l"(y), "r"(addr)
+                 : "memory");
+}
+
+// Each lane eliminates its own rows; a step is one 128-bit CAS that claims an
+// empty slot or returns the stored (row, right-hand side).
+// Stream staged rows [lo, hi) (index range) into the band; stored ring
+// indices are appended to S.clist (S.ncommit).  Returns kOk, kDependent or
+// kOverflow; nothing is rolled back here.  Every lane eliminates its own row
+// (one slot_cas per step) and takes the next row when its row is stored.
+__device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
+    if (hi <= lo) return kOk;
+    if (lane == 0) {
+        S.next = lo + 32u;
+        S.flag = 0;
+    }
+    __syncwarp();
+    uint32_t idx = lo + (uint32_t)lane;
+    bool has = idx < hi;
+    unsigned long long cur = 0, y = 0;
+    uint32_t pos = 0;
+    if (has) {
+        cur = S.rc[idx];
+        y = kYValid | S.ry[idx];
+        pos = bB + S.ro[idx];
+    }
+    volatile uint32_t *vflag = &S.flag;
+    while (has) {
+        unsigned long long oc, oy;
+        slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
+        if (oc == 0ull) {
+            S.clist[atomicAdd(&S.ncommit, 1u)] = (uint16_t)(pos & kRingMask);
+            has = false;
+            if (*vflag == 0u) {
+                idx = atomicAdd(&S.next, 1u);
+                if (idx < hi) {
+                    cur = S.rc[idx];
+                    y = kYValid | S.ry[idx];
+                    pos = bB + S.ro[idx];
+                    has = true;
                 }
             }
-            const bool any_fail = __any_sync(kFull, fail);
-            const bool any_ovf = __any_sync(kFull, ovf);
-            if (any_fail || any_ovf) {
-                rollback(S, ncommit, lane);
-                if (any_ovf) {
-                    if (lane == 0) atomicOr(a.err, kErrRingOverflow);
-                    return kOverflow;
-                }
-                return kDependent;
-            }
-            // claim the landing slots; one claimant per slot wins
-#pragma unroll
-            for (int k = 0; k < kRPL; ++k)
-                if (act & (1u << k)) S.claim[pos[k] & kRingMask] = (uint16_t)(lane * kRPL + k);
-            __syncwarp();
-            uint32_t win = 0;
-#pragma unroll
-            for (int k = 0; k < kRPL; ++k)
-                if ((act & (1u << k)) && S.claim[pos[k] & kRingMask] == (uint16_t)(lane * kRPL + k))
-                    win |= 1u << k;
-            __syncwarp();
-            const uint32_t nw = __popc(win);
-            uint32_t incl = nw;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, d);
-                if (lane >= d) incl += t;
-            }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            uint32_t o = ncommit + incl - nw;
-#pragma unroll
-            for (int k = 0; k < kRPL; ++k) {
-                if (win & (1u << k)) {
-                    const uint32_t ri = pos[k] & kRingMask;
-                    S.C[ri] = cur[k];
-                    S.Y[ri] = y[k];
-                    S.clist[o++] = (uint16_t)ri;
-                }
-            }
-            ncommit += total;
-            act &= ~win;
-            __syncwarp();
+            continue;
+        }
+        cur ^= oc;
+        y ^= oy & ~kYValid;
+        if (cur == 0ull) {
+            atomicOr(&S.flag, 1u);
+            break;
+        }
+        const uint32_t lo32 = (uint32_t)cur;
+        const int tz = lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(cur >> 32));
+        cur >>= tz;
+        pos += (uint32_t)tz;
+        if (pos - bB >= (uint32_t)kRing) {
+            atomicOr(&S.flag, 2u);
+            break;
+        }
+    }
+    __syncwarp();
+    const uint32_t f = S.flag;
+    return (f & 2u) ? kOverflow : ((f & 1u) ? kDependent : kOk);
+}
+
+// Insert the rows of bucket [rs, re) whose offset lies in [olo, ohi) as one
+// set; on a dependency or overflow every row this call stored is removed.
+template <typename V>
+__device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, uint32_t rs, uint32_t re, uint32_t bB,
+                          uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
+    if (lane == 0) S.ncommit = 0;
+    __syncwarp();
+    for (uint32_t base = rs; base < re; base += kStage) {
+        const uint32_t cnt = min((uint32_t)kStage, re - base);
+        if (staged_base != base) {
+            stage_rows(S, a, base, cnt, bB, lane);
+            staged_base = base;
+        }
+        const int rc = stream_insert(S, S.first[olo], S.first[ohi], bB, lane);
+        if (rc != kOk) {
+            rollback(S, S.ncommit, lane);
+            if (rc == kOverflow && lane == 0) atomicOr(a.err, kErrRingOverflow);
+            return rc;
         }
     }
     return kOk;
@@ -215,10 +281,10 @@ __device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, uin
     __syncwarp();
     for (uint64_t s = from + lane; s < to; s += 32) {
         const uint32_t ri = (uint32_t)s & kRingMask;
-        a.Cg[s] = S.C[ri];
-        a.Yg[s] = (V)S.Y[ri];
-        S.C[ri] = 0;
-        S.Y[ri] = 0;
+        a.Cg[s] = S.ring[ri].c;
+        a.Yg[s] = (V)(S.ring[ri].y & 0xffffffffull);
+        S.ring[ri].c = 0;
+        S.ring[ri].y = 0;
     }
     __syncwarp();
 }
@@ -238,8 +304,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     const uint64_t own_hi = part == L.K - 1 ? L.m : (part + 1) * L.P + kW;
 
     for (int i = lane; i < kRing; i += 32) {
-        S.C[i] = 0;
-        S.Y[i] = 0;
+        S.ring[i].c = 0;
+        S.ring[i].y = 0;
     }
     __syncwarp();
 
@@ -262,7 +328,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         uint32_t code = cut ? fcode : 0;
         const uint32_t rs = a.bstart[b], re = a.bstart[b + 1];
         if (re > rs) {
-            int rc = insert_set(S, a, rs, re, (uint32_t)bB, forced, L.B, lane);
+            uint32_t staged = 0xffffffffu;
+            int rc = insert_set(S, a, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
             if (rc == kOverflow) return;
             if (rc == kDependent) {
                 if (L.fallback) {
@@ -273,7 +340,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                 for (int k = 2; k >= 0; --k) {
                     if (lv[k + 1] <= forced) break;
                     const uint32_t lo = max(lv[k], forced), hi = lv[k + 1];
-                    const int rc2 = insert_set(S, a, rs, re, (uint32_t)bB, lo, hi, lane);
+                    const int rc2 = insert_set(S, a, rs, re, (uint32_t)bB, lo, hi, staged, lane);
                     if (rc2 == kOverflow) return;
                     if (rc2 == kDependent) {
                         code = (uint32_t)k + 1;
@@ -301,10 +368,24 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
 
 // Back-substitution, right to left over the partition's owned slots, one
 // lane per value bit: Z[i] = Y[i] ^ parity((C[i] >> 1) & Z[i+1 .. i+63]),
-// Z[i] = 0 on empty slots (C = Y = 0 there).  The 64-bit register `st` holds
-// Z of the 64 slots to the right of the current one; after a block of 64
-// slots it is exactly that block's table word for this bit plane.
+// Z[i] = 0 on empty slots (C = Y = 0 there).  The 64-bit register T holds Z of
+// the 64 slots right of the current group (bit j = slot i+1+j); after a block
+// of 64 slots it is exactly that block's table word for this bit plane.
+//
+// Four slots are solved per step so that the dependent chain is short: with
+// c'_s = C[s] >> 1, the four parities against T are independent,
+//   A_d = Y[i-d] ^ parity((c'_{i-d} >> d) & T),  d = 0..3,
+// and the slots of the group then correct each other through the low bits of
+// their own rows:
+//   z_i = A_0,  z_{i-1} = A_1 ^ c'_{i-1}[0] z_i,
+//   z_{i-2} = A_2 ^ c'_{i-2}[0] z_{i-1} ^ c'_{i-2}[1] z_i,
+//   z_{i-3} = A_3 ^ c'_{i-3}[0] z_{i-2} ^ c'_{i-3}[1] z_{i-1} ^ c'_{i-3}[2] z_i,
+//   T <- (T << 4) | z_i z_{i-1} z_{i-2} z_{i-3}.
 constexpr int kBsWarps = 4;
+
+__device__ __forceinline__ uint32_t parity64(uint64_t x) {
+    return (uint32_t)__popc((uint32_t)x ^ (uint32_t)(x >> 32)) & 1u;
+}
 
 template <typename V>
 __global__ void __launch_bounds__(32 * kBsWarps)
@@ -318,7 +399,7 @@ k_backsub(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg
     const uint64_t own_hi = part == L.K - 1 ? L.m : (part + 1) * L.P + kW;
     const uint64_t blo = own_lo >> 6, bhi = own_hi >> 6;
     if (bhi <= blo) return;
-    uint64_t st = 0;
+    uint64_t T = 0;
     // software pipeline: registers hold the next block while this one is solved
     uint64_t nc0 = Cg[((bhi - 1) << 6) + lane], nc1 = Cg[((bhi - 1) << 6) + lane + 32];
     uint32_t ny0 = Yg[((bhi - 1) << 6) + lane], ny1 = Yg[((bhi - 1) << 6) + lane + 32];
@@ -337,13 +418,22 @@ k_backsub(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg
             ny1 = Yg[s0 + lane + 32];
         }
         if ((uint32_t)lane < L.r) {
-#pragma unroll 16
-            for (int i = 63; i >= 0; --i) {
-                const uint64_t c = sc[warp][i];
-                const uint32_t z = ((sy[warp][i] >> lane) & 1u) ^ (__popcll(c & st) & 1u);
-                st = (st << 1) | z;
+#pragma unroll 4
+            for (int g = 15; g >= 0; --g) {
+                const int i = 4 * g + 3;
+                const uint64_t c0 = sc[warp][i], c1 = sc[warp][i - 1], c2 = sc[warp][i - 2], c3 = sc[warp][i - 3];
+                const uint32_t a0 = ((sy[warp][i] >> lane) & 1u) ^ parity64(c0 & T);
+                const uint32_t a1 = ((sy[warp][i - 1] >> lane) & 1u) ^ parity64((c1 >> 1) & T);
+                const uint32_t a2 = ((sy[warp][i - 2] >> lane) & 1u) ^ parity64((c2 >> 2) & T);
+                const uint32_t a3 = ((sy[warp][i - 3] >> lane) & 1u) ^ parity64((c3 >> 3) & T);
+                const uint32_t l1 = (uint32_t)c1, l2 = (uint32_t)c2, l3 = (uint32_t)c3;
+                const uint32_t z0 = a0;
+                const uint32_t z1 = a1 ^ (l1 & z0);
+                const uint32_t z2 = a2 ^ ((l2 >> 1) & z0) ^ (l2 & z1);
+                const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
+                T = (T << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
             }
-            Z[blk * L.r + lane] = st;
+            Z[blk * L.r + lane] = T;
         }
     }
 }
