@@ -196,8 +196,9 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
  * an interface convenience of this library.)
  *   Arguments, layout and result are those of burr_stage_sort; all pointers
  *   are device memory owned by the caller.
- *   n must be <= BURR_NOALLOC_MAX_KEYS, else BURR_ERR_INVALID with a message.
- *   The sort's scratch is one fixed file-scope device array of about 12.8 MB
+ *   n must be <= BURR_NOALLOC_MAX_KEYS and m <= BURR_NOALLOC_MAX_SLOTS, else
+ *   BURR_ERR_INVALID with a message.
+ *   The sort's scratch is one fixed file-scope device array of about 12.6 MB
  *   that every GPU which loads the library keeps until the process exits.
  *   The first call on a device looks up that array's device address (once per
  *   device, with the device current); make that first call before any stream
@@ -206,6 +207,7 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
  *   threads) race, so order them, e.g. on one stream.
  */
 #define BURR_NOALLOC_MAX_KEYS (1u << 20)
+#define BURR_NOALLOC_MAX_SLOTS (1u << 24)
 int burr_stage_sort_noalloc(const uint64_t *d_keys, const void *d_values, uint64_t n, uint32_t r,
                             uint64_t seed, uint32_t layer_index, uint64_t m,
                             uint64_t *d_sorted_keys, void *d_sorted_values, uint32_t *d_bucket_start,

@@ -345,7 +345,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side), "backsub");
         tev[l][4] = tm.mark_on(side.side);
         CK(side.solved(set), "order");
-        h->launches += kSortKernels + 2;
+        h->launches += sort_kernel_count(L) + 2;
         unsigned long long hc[2] = {0, 0};
         CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
         CK(cudaStreamSynchronize(st), "layer");
@@ -398,7 +398,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             const int t1 = tm.mark();
             CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
                            nullptr, nullptr, nullptr, bcount, err, st), "band");
-            h->launches += kSortKernels + 1;
+            h->launches += sort_kernel_count(L) + 1;
             uint32_t he = 0;
             CK(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
             CK(cudaStreamSynchronize(st), "base case");

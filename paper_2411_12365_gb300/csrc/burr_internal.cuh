@@ -58,14 +58,10 @@ struct LayerDesc {
     uint32_t vmask;      // (1 << r) - 1
 };
 
-// Sorting by bucket: level-1 bins of 2^shift1 start slots, level-2 buckets.
-struct SortPlan {
-    uint32_t shift1;     // log2 start slots per level-1 bin
-    uint32_t nbins1;     // level-1 bins
-};
-
-constexpr uint64_t kSortKernels = 4;   // kernels one launch_sort enqueues (n > 0)
+// Scratch bytes of launch_sort for n keys in a layer of m slots.
 size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes);
+// Kernels one launch_sort of this layer enqueues (n > 0).
+uint32_t sort_kernel_count(const LayerDesc &L);
 
 // Sort n (key, value) pairs of a layer into bucket order.
 // scratch: sort_scratch_bytes(n, m, vbytes) bytes of device memory.

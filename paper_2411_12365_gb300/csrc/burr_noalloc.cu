@@ -6,7 +6,7 @@
 // and unpredictable latency of cudaMalloc/cudaFree, or code that must not run
 // out of memory half-way through a pipeline.
 //
-// The sort's scratch (the level-1 scatter buffers and the bin counters) lives
+// The sort's scratch (the scatter buffer and the digit and group counters) lives
 // in one file-scope device array of fixed size.  Every GPU that loads the
 // library holds this array until the process exits.  All calls share it and
 // it keeps the contents of the last call, so calls whose work overlaps on the
@@ -21,14 +21,18 @@
 namespace {
 
 constexpr uint64_t kNoAllocMaxKeys = BURR_NOALLOC_MAX_KEYS;
-constexpr size_t kBins = 16385;   // level-1 bins + 1 (the sort plan never needs more)
+constexpr uint64_t kNoAllocMaxSlots = BURR_NOALLOC_MAX_SLOTS;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// level-1 keys (8 B) and values (<= 4 B) of up to kNoAllocMaxKeys keys, plus
-// three bin arrays; this is burr::sort_scratch_bytes(kNoAllocMaxKeys, ., 4).
-constexpr size_t kScratchBytes =
-    align256(kNoAllocMaxKeys * 8) + align256(kNoAllocMaxKeys * 4) + 3 * align256(kBins * 4);
+// burr::sort_scratch_bytes(kNoAllocMaxKeys, kNoAllocMaxSlots, 4): the scatter
+// buffer of the keys (8 B) and values (<= 4 B), three arrays of pass-1 digit
+// counters, and three arrays of per-group counters (groups of 64 buckets of at
+// least 64 slots).
+constexpr size_t kDigits = 1024 + 1;
+constexpr size_t kGroups = ((kNoAllocMaxSlots - 64 + 128) / 64 + 63) / 64 + 1 + 1;
+constexpr size_t kScratchBytes = align256(kNoAllocMaxKeys * 8) + align256(kNoAllocMaxKeys * 4) +
+                                 3 * align256(kDigits * 4) + 3 * align256(kGroups * 4);
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
@@ -69,8 +73,9 @@ int burr_stage_sort_noalloc(const uint64_t *d_keys, const void *d_values, uint64
     if (n > kNoAllocMaxKeys)
         return set_error(BURR_ERR_INVALID, ("n = " + std::to_string(n) + " exceeds the allocation-free limit of " +
                                             std::to_string(kNoAllocMaxKeys) + " keys; use burr_stage_sort").c_str());
-    if (m < kW || m % 64 || m >= (1ull << 32))
-        return set_error(BURR_ERR_INVALID, "m must be a multiple of 64 in [64, 2^32)");
+    if (m < kW || m % 64 || m > kNoAllocMaxSlots)
+        return set_error(BURR_ERR_INVALID, ("m must be a multiple of 64 in [64, " +
+                                            std::to_string(kNoAllocMaxSlots) + "] (allocation-free limit)").c_str());
     if (n && (!d_keys || !d_values || !d_sorted_keys || !d_sorted_values))
         return set_error(BURR_ERR_INVALID, "NULL argument");
     if (!d_bucket_start) return set_error(BURR_ERR_INVALID, "NULL bucket offsets");

@@ -1,16 +1,22 @@
 // burr_sort.cu -- "sort the hashes by their insertion position" (Sec. 4; the
-// paper uses the CPU sorter IPS2Ra).  On the GPU the build only needs the
-// equations grouped by bucket (start / B) in ascending bucket order: the order
-// inside a bucket is free, because the band kernel inserts a bucket's rows as a
-// set (any order inside a threshold band gives the same kept set and, with free
-// slots fixed to 0, the same table).  So this is a two-pass MSD counting sort
-// on the bucket id:
-//   level 1: bins of 2^bshift1 buckets (<= 16384 bins), shared-memory
-//            histograms per CTA, one global atomic per (tile, bin);
-//   level 2: one CTA per level-1 bin counting-sorts its records by bucket in
-//            shared memory and writes the bucket offsets.
-// The equation is recomputed from the key in each pass (hash fused into the
-// consumer) instead of materialising 16-byte records.
+// paper uses the CPU sorter IPS2Ra).  The build only needs the equations
+// grouped by bucket (start / B) in ascending bucket order: the order inside a
+// bucket is free, because the band kernel inserts a bucket's rows as a set
+// (any order inside a threshold band gives the same kept set and, with free
+// slots fixed to 0, the same table).  So this is an MSD counting sort on the
+// bucket id, shaped for HBM:
+//
+//   * groups of 64 buckets (about 8k keys) are the unit of the last pass;
+//   * one or two scatter passes bring the keys into group order.  Each pass
+//     works in tiles of 4096 keys: a shared-memory histogram and scan order
+//     the tile by digit in shared memory, one global atomic per (tile, digit)
+//     reserves the output range, and the tile is written out as contiguous
+//     runs per digit (coalesced stores, not scattered 8-byte writes);
+//   * the last pass sorts each group in shared memory (count, scan, place)
+//     and writes it out in order, together with the bucket offsets.
+//
+// The equation is recomputed from the key in every pass (the hash is fused
+// into its consumers) instead of materialising 16-byte records.
 #include <cstdio>
 
 #include "burr_internal.cuh"
@@ -19,22 +25,19 @@ namespace burr {
 
 namespace {
 
-constexpr int kL1Threads = 256;
-constexpr int kL1Items = 16;                       // tile = 4096 keys
-constexpr int kL1Tile = kL1Threads * kL1Items;
-constexpr uint32_t kMaxBins1 = 16384;
-constexpr int kL2Threads = 512;
-constexpr uint32_t kMaxBucketsPerBin = 4096;
+constexpr int kGroupShift = 6;                  // 64 buckets per group
+constexpr uint32_t kGroupBuckets = 1u << kGroupShift;
+constexpr int kHistThreads = 256;
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = 16;
+constexpr int kTile = kTileThreads * kTileItems; // 4096 keys per tile
+constexpr uint32_t kMaxDigits = 1024;           // digits of one scatter pass
+constexpr int kGroupThreads = 512;
+constexpr uint32_t kGroupCap = 12288;           // keys a group may hold to be sorted in shared memory
 
 inline uint32_t ceil_log2(uint64_t x) {
     uint32_t l = 0;
     while ((1ull << l) < x) ++l;
-    return l;
-}
-
-inline uint32_t log2_exact(uint32_t x) {
-    uint32_t l = 0;
-    while ((1u << l) < x) ++l;
     return l;
 }
 
@@ -49,119 +52,90 @@ int num_sms() {
     return sms;
 }
 
-__global__ void __launch_bounds__(kL1Threads)
-k_l1_hist(const uint64_t *__restrict__ keys, uint64_t n, uint64_t sigma, uint64_t range,
-          uint32_t shift, uint32_t nbins, uint32_t *__restrict__ counts) {
-    extern __shared__ uint32_t sh[];
-    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
+// Digits of the scatter passes.  group = start >> gshift.  One pass when the
+// groups fit one pass's digits; otherwise pass 1 uses the top d1 bits of the
+// group id and pass 2 the low d2 bits inside each pass-1 bin.
+struct Plan {
+    uint32_t log2B, gshift;
+    uint64_t ngroups;
+    int passes;          // 0 (one group), 1 or 2
+    uint32_t d2;         // low group bits sorted by pass 2
+    uint32_t D1, D2;     // digits of pass 1 and pass 2
+};
+
+Plan make_plan(const LayerDesc &L) {
+    Plan p;
+    p.log2B = ceil_log2(L.B);
+    p.gshift = p.log2B + kGroupShift;
+    p.ngroups = (L.nb + kGroupBuckets - 1) / kGroupBuckets;
+    if (p.ngroups <= 1) {
+        p.passes = 0;
+        p.d2 = 0;
+        p.D1 = p.D2 = 1;
+    } else if (p.ngroups <= kMaxDigits) {
+        p.passes = 1;
+        p.d2 = 0;
+        p.D1 = (uint32_t)p.ngroups;
+        p.D2 = 1;
+    } else {
+        const uint32_t bits = ceil_log2(p.ngroups);
+        p.passes = 2;
+        p.d2 = bits / 2;
+        p.D2 = 1u << p.d2;
+        p.D1 = (uint32_t)((p.ngroups + p.D2 - 1) >> p.d2);
+    }
+    return p;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__device__ __forceinline__ uint32_t group_of(uint64_t key, uint64_t sigma, uint64_t range, uint32_t gshift) {
+    return start_slot(key, sigma, range) >> gshift;
+}
+
+// counts[digit] of every key, digit = group >> dshift.
+__global__ void __launch_bounds__(kHistThreads)
+k_hist(const uint64_t *__restrict__ keys, uint64_t n, uint64_t sigma, uint64_t range, uint32_t gshift,
+       uint32_t dshift, uint32_t D, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t sh[kMaxDigits];
+    for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        atomicAdd(&sh[start_slot(keys[i], sigma, range) >> shift], 1u);
+        atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) >> dshift], 1u);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x)
+    for (uint32_t i = threadIdx.x; i < D; i += blockDim.x)
         if (sh[i]) atomicAdd(&counts[i], sh[i]);
 }
 
-// Exclusive scan of nbins counts into off[0..nbins] and cursor[0..nbins).
+// Per pass-1 bin (segment), counts of its low group bits: counts[group].
+__global__ void __launch_bounds__(kHistThreads)
+k_hist_seg(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ off1, uint32_t nseg_ctas,
+           uint64_t sigma, uint64_t range, uint32_t gshift, uint32_t D2, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t sh[kMaxDigits];
+    const uint32_t seg = blockIdx.x / nseg_ctas, part = blockIdx.x % nseg_ctas;
+    for (uint32_t i = threadIdx.x; i < D2; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t lo = off1[seg], hi = off1[seg + 1];
+    for (uint32_t i = lo + part * blockDim.x + threadIdx.x; i < hi; i += nseg_ctas * blockDim.x)
+        atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) & (D2 - 1)], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < D2; i += blockDim.x)
+        if (sh[i]) atomicAdd(&counts[(uint64_t)seg * D2 + i], sh[i]);
+}
+
+// Exclusive scan of counts[0..len) into off[0..len] and cursor[0..len), one block.
 __global__ void __launch_bounds__(1024)
-k_scan_bins(const uint32_t *__restrict__ counts, uint32_t nbins, uint32_t *__restrict__ off,
-            uint32_t *__restrict__ cursor) {
+k_scan(const uint32_t *__restrict__ counts, uint32_t len, uint32_t *__restrict__ off, uint32_t *__restrict__ cursor) {
     __shared__ uint32_t warp_sums[32];
-    const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = threadIdx.x * per;
-    uint32_t local = 0;
-    for (uint32_t i = lo; i < lo + per && i < nbins; ++i) local += counts[i];
-    // block exclusive scan of `local`
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = local;
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-            if (lane >= d) s += y;
-        }
-        warp_sums[lane] = s;
-    }
-    __syncthreads();
-    uint32_t run = x - local + (warp ? warp_sums[warp - 1] : 0);
-    for (uint32_t i = lo; i < lo + per && i < nbins; ++i) {
-        off[i] = run;
-        cursor[i] = run;
-        run += counts[i];
-    }
-    if (threadIdx.x == blockDim.x - 1) off[nbins] = run;
-}
-
-template <typename V>
-__global__ void __launch_bounds__(kL1Threads)
-k_l1_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
-             uint64_t sigma, uint64_t range, uint32_t shift, uint32_t nbins,
-             uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out, V *__restrict__ vals_out) {
-    extern __shared__ uint32_t sh[];
-    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    const uint64_t ntiles = (n + kL1Tile - 1) / kL1Tile;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t base = tile * kL1Tile + threadIdx.x;
-        uint64_t key[kL1Items];
-        V val[kL1Items];
-        uint32_t bin[kL1Items], rank[kL1Items];
-#pragma unroll
-        for (int j = 0; j < kL1Items; ++j) {
-            const uint64_t i = base + (uint64_t)j * kL1Threads;
-            if (i < n) {
-                key[j] = keys[i];
-                val[j] = vals[i];
-                bin[j] = start_slot(key[j], sigma, range) >> shift;
-                rank[j] = atomicAdd(&sh[bin[j]], 1u);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kL1Items; ++j) {
-            const uint64_t i = base + (uint64_t)j * kL1Threads;
-            if (i < n && rank[j] == 0) {
-                const uint32_t cnt = sh[bin[j]];
-                sh[bin[j]] = atomicAdd(&cursor[bin[j]], cnt);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kL1Items; ++j) {
-            const uint64_t i = base + (uint64_t)j * kL1Threads;
-            if (i < n) {
-                const uint32_t pos = sh[bin[j]] + rank[j];
-                keys_out[pos] = key[j];
-                vals_out[pos] = val[j];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kL1Items; ++j) {
-            const uint64_t i = base + (uint64_t)j * kL1Threads;
-            if (i < n) sh[bin[j]] = 0;
-        }
-        __syncthreads();
-    }
-}
-
-// Block-wide exclusive scan over cnt[0..len) (len <= kMaxBucketsPerBin) in place.
-__device__ void block_exclusive_scan(uint32_t *cnt, uint32_t len, uint32_t *warp_sums) {
     const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = threadIdx.x * per;
     uint32_t local = 0;
-    for (uint32_t i = lo; i < lo + per && i < len; ++i) local += cnt[i];
+    for (uint32_t i = lo; i < lo + per && i < len; ++i) local += counts[i];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = local;
     for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
         if (lane >= d) x += y;
     }
     if (lane == 31) warp_sums[warp] = x;
@@ -169,7 +143,7 @@ __device__ void block_exclusive_scan(uint32_t *cnt, uint32_t len, uint32_t *warp
     if (warp == 0) {
         uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
         for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
             if (lane >= d) s += y;
         }
         warp_sums[lane] = s;
@@ -177,98 +151,272 @@ __device__ void block_exclusive_scan(uint32_t *cnt, uint32_t len, uint32_t *warp
     __syncthreads();
     uint32_t run = x - local + (warp ? warp_sums[warp - 1] : 0);
     for (uint32_t i = lo; i < lo + per && i < len; ++i) {
-        const uint32_t c = cnt[i];
-        cnt[i] = run;
-        run += c;
+        off[i] = run;
+        cursor[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) off[len] = run;
+}
+
+// Block-wide exclusive scan of cnt[0..len) (len <= kMaxDigits) into out[].
+__device__ void block_scan(const uint32_t *cnt, uint32_t *out, uint32_t len, uint32_t *warp_sums) {
+    const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = threadIdx.x * per;
+    uint32_t local = 0;
+    for (uint32_t i = lo; i < lo + per && i < len; ++i) local += cnt[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = local;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t run = x - local + (warp ? warp_sums[warp - 1] : 0);
+    for (uint32_t i = lo; i < lo + per && i < len; ++i) {
+        out[i] = run;
+        run += cnt[i];
     }
     __syncthreads();
 }
 
-template <typename V>
-__global__ void __launch_bounds__(kL2Threads)
-k_l2_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals,
-          const uint32_t *__restrict__ off1, uint64_t sigma, uint64_t range, uint32_t log2B,
-          uint32_t bshift1, uint64_t nb, uint64_t *__restrict__ keys_out, V *__restrict__ vals_out,
-          uint32_t *__restrict__ bucket_start) {
-    __shared__ uint32_t hist[kMaxBucketsPerBin];
-    __shared__ uint32_t warp_sums[32];
-    const uint64_t b_lo = (uint64_t)blockIdx.x << bshift1;
-    const uint32_t nbk = (uint32_t)min((uint64_t)1 << bshift1, nb - b_lo);
-    const uint32_t lo = off1[blockIdx.x], hi = off1[blockIdx.x + 1];
-    for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const uint32_t b = (start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo;
-        atomicAdd(&hist[b], 1u);
+// One scatter pass.  Tiles of kTile keys are ordered by digit in shared
+// memory and written as contiguous runs.  Unsegmented (pass 1): digit =
+// group >> dshift over all n keys, cursor[digit].  Segmented (pass 2): tiles
+// stay inside pass-1 bin seg = blockIdx / nseg_ctas, digit = group & (D - 1),
+// cursor[seg * D + digit] (= cursor[group]).
+template <typename V, bool SEG>
+__global__ void __launch_bounds__(kTileThreads)
+k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
+          const uint32_t *__restrict__ off1, uint32_t nseg_ctas, uint64_t sigma, uint64_t range, uint32_t gshift,
+          uint32_t dshift, uint32_t D, uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out,
+          V *__restrict__ vals_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
+    V *sval = reinterpret_cast<V *>(skey + kTile);
+    uint16_t *sdig = reinterpret_cast<uint16_t *>(sval + kTile);
+    __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
+
+    uint64_t lo = 0, hi = n;
+    uint32_t seg = 0, part = blockIdx.x, nparts = gridDim.x;
+    if (SEG) {
+        seg = blockIdx.x / nseg_ctas;
+        part = blockIdx.x % nseg_ctas;
+        nparts = nseg_ctas;
+        lo = off1[seg];
+        hi = off1[seg + 1];
     }
+    for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    block_exclusive_scan(hist, nbk, warp_sums);
-    for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bucket_start[b_lo + i] = lo + hist[i];
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) bucket_start[nb] = hi;
-    __syncthreads();
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const uint64_t key = keys[i];
-        const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
-        const uint32_t pos = lo + atomicAdd(&hist[b], 1u);
-        keys_out[pos] = key;
-        vals_out[pos] = vals[i];
+    const uint64_t ntiles = (hi - lo + kTile - 1) / kTile;
+    for (uint64_t t = part; t < ntiles; t += nparts) {
+        const uint64_t base = lo + t * kTile;
+        const uint32_t cnt = (uint32_t)min((uint64_t)kTile, hi - base);
+        uint64_t key[kTileItems];
+        V val[kTileItems];
+        uint32_t dig[kTileItems], rank[kTileItems];
+#pragma unroll
+        for (int j = 0; j < kTileItems; ++j) {
+            const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
+            if (i < cnt) {
+                key[j] = keys[base + i];
+                val[j] = vals[base + i];
+                const uint32_t g = group_of(key[j], sigma, range, gshift);
+                dig[j] = SEG ? (g & (D - 1)) : (g >> dshift);
+                rank[j] = atomicAdd(&hist[dig[j]], 1u);
+            }
+        }
+        __syncthreads();
+        block_scan(hist, excl, D, warp_sums);
+        for (uint32_t d = threadIdx.x; d < D; d += blockDim.x)
+            if (hist[d]) gbase[d] = atomicAdd(&cursor[(uint64_t)seg * (SEG ? D : 0) + d], hist[d]);
+#pragma unroll
+        for (int j = 0; j < kTileItems; ++j) {
+            const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
+            if (i < cnt) {
+                const uint32_t p = excl[dig[j]] + rank[j];
+                skey[p] = key[j];
+                sval[p] = val[j];
+                sdig[p] = (uint16_t)dig[j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t d = sdig[i];
+            const uint32_t dst = gbase[d] + (i - excl[d]);
+            keys_out[dst] = skey[i];
+            vals_out[dst] = sval[i];
+        }
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < D; d += blockDim.x) hist[d] = 0;
+        __syncthreads();
     }
 }
 
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
+// Last pass: one block per group of 64 buckets.  The group's keys are
+// counted per bucket, placed into bucket order in shared memory and written
+// out contiguously; the bucket offsets are written too.  A group larger than
+// the shared-memory capacity is placed directly in global memory instead.
 template <typename V>
-cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, uint64_t *keys_out,
-                      V *vals_out, uint32_t *bucket_start, void *scratch, cudaStream_t st) {
-    const uint64_t n = L.n;
-    const uint32_t log2B = log2_exact(L.B);
-    const uint32_t bshift1 = (uint32_t)max(9, (int)ceil_log2(L.nb) - 14);
-    const uint32_t shift = log2B + bshift1;
-    const uint32_t nbins = (uint32_t)((L.nb + (1ull << bshift1) - 1) >> bshift1);
-    if (nbins > kMaxBins1 || (1u << bshift1) > kMaxBucketsPerBin) return cudaErrorInvalidValue;
+__global__ void __launch_bounds__(kGroupThreads)
+k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, const uint32_t *__restrict__ goff,
+             uint64_t sigma, uint64_t range, uint32_t log2B, uint64_t nb, uint64_t *__restrict__ keys_out,
+             V *__restrict__ vals_out, uint32_t *__restrict__ bucket_start) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
+    V *sval = reinterpret_cast<V *>(skey + kGroupCap);
+    __shared__ uint32_t cnt[kGroupBuckets], cur[kGroupBuckets], warp_sums[32];
+    const uint64_t g = blockIdx.x;
+    const uint64_t b_lo = g << kGroupShift;
+    const uint32_t nbk = (uint32_t)min((uint64_t)kGroupBuckets, nb - b_lo);
+    const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
+    if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    __syncthreads();
+    block_scan(cnt, cur, kGroupBuckets, warp_sums);
+    if (threadIdx.x < nbk) bucket_start[b_lo + threadIdx.x] = lo + cur[threadIdx.x];
+    if (g == gridDim.x - 1 && threadIdx.x == 0) bucket_start[nb] = hi;
+    __syncthreads();
+    if (n <= kGroupCap) {
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const uint64_t key = keys[i];
+            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t p = atomicAdd(&cur[b], 1u);
+            skey[p] = key;
+            sval[p] = vals[i];
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            keys_out[lo + i] = skey[i];
+            vals_out[lo + i] = sval[i];
+        }
+    } else {
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const uint64_t key = keys[i];
+            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t p = lo + atomicAdd(&cur[b], 1u);
+            keys_out[p] = key;
+            vals_out[p] = vals[i];
+        }
+    }
+}
 
+struct Scratch {
+    uint64_t *keys;
+    void *vals;
+    uint32_t *c1, *o1, *u1;      // pass-1 counts, offsets, cursors (kMaxDigits + 1)
+    uint32_t *c2, *o2, *u2;      // per-group counts, offsets (= group offsets), cursors
+};
+
+Scratch carve(void *scratch, uint64_t n, uint64_t ngroups, uint32_t vbytes) {
+    Scratch s;
     char *p = (char *)scratch;
-    uint64_t *k1 = (uint64_t *)p;  p += align256(n * 8);
-    V *v1 = (V *)p;                p += align256(n * sizeof(V));
-    uint32_t *counts = (uint32_t *)p; p += align256((kMaxBins1 + 1) * 4);
-    uint32_t *off1 = (uint32_t *)p;   p += align256((kMaxBins1 + 1) * 4);
-    uint32_t *cursor = (uint32_t *)p;
+    s.keys = (uint64_t *)p;  p += align256(n * 8);
+    s.vals = p;              p += align256(n * vbytes);
+    s.c1 = (uint32_t *)p;    p += align256((kMaxDigits + 1) * 4);
+    s.o1 = (uint32_t *)p;    p += align256((kMaxDigits + 1) * 4);
+    s.u1 = (uint32_t *)p;    p += align256((kMaxDigits + 1) * 4);
+    s.c2 = (uint32_t *)p;    p += align256((ngroups + 1) * 4);
+    s.o2 = (uint32_t *)p;    p += align256((ngroups + 1) * 4);
+    s.u2 = (uint32_t *)p;
+    return s;
+}
 
-    cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nbins * 4, st);
-    if (e != cudaSuccess) return e;
-    const size_t smem1 = (size_t)nbins * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_l1_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins1 * 4);
-        cudaFuncSetAttribute(k_l1_scatter<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins1 * 4);
-        cudaFuncSetAttribute(k_l1_scatter<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins1 * 4);
-        cudaFuncSetAttribute(k_l1_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins1 * 4);
-        attr_set = true;
-    }
+template <typename V>
+cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, uint64_t *keys_out, V *vals_out,
+                      uint32_t *bucket_start, void *scratch, cudaStream_t st) {
+    const uint64_t n = L.n;
+    const Plan P = make_plan(L);
+    Scratch S = carve(scratch, n, P.ngroups, sizeof(V));
     const unsigned sms = (unsigned)num_sms();
-    k_l1_hist<<<grid_for(n, kL1Threads * 8, sms * 4), kL1Threads, smem1, st>>>(
-        keys, n, L.sigma, L.range, shift, nbins, counts);
-    k_scan_bins<<<1, 1024, 0, st>>>(counts, nbins, off1, cursor);
-    k_l1_scatter<V><<<grid_for(n, kL1Tile, sms * 4), kL1Threads, smem1, st>>>(
-        keys, vals, n, L.sigma, L.range, shift, nbins, cursor, k1, v1);
-    k_l2_sort<V><<<nbins, kL2Threads, 0, st>>>(k1, v1, off1, L.sigma, L.range, log2B, bshift1, L.nb,
-                                               keys_out, vals_out, bucket_start);
+    const size_t tile_smem = (size_t)kTile * (8 + sizeof(V) + 2);
+    const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_scatter<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_scatter<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_group_sort<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
+    if (e != cudaSuccess) return e;
+
+    const uint32_t *goff;
+    const uint64_t *gk = keys;   // input of the group pass
+    const V *gv = vals;
+    if (P.passes == 0) {
+        // one group: offsets [0, n]
+        const uint32_t h[2] = {0, (uint32_t)n};
+        e = cudaMemcpyAsync(S.o2, h, sizeof(h), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        goff = S.o2;
+    } else if (P.passes == 1) {
+        e = cudaMemsetAsync(S.c1, 0, (size_t)P.D1 * 4, st);
+        if (e != cudaSuccess) return e;
+        k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
+                                                                                    P.gshift, 0, P.D1, S.c1);
+        k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
+        k_scatter<V, false><<<grid_for(n, kTile, sms * 3), kTileThreads, tile_smem, st>>>(
+            keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, 0, P.D1, S.u1, S.keys, (V *)S.vals);
+        goff = S.o1;
+        gk = S.keys;
+        gv = (const V *)S.vals;
+    } else {
+        // pass 1 into the caller's output buffers, pass 2 into scratch
+        e = cudaMemsetAsync(S.c1, 0, (size_t)P.D1 * 4, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(S.c2, 0, (size_t)P.ngroups * 4, st);
+        if (e != cudaSuccess) return e;
+        k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
+                                                                                    P.gshift, P.d2, P.D1, S.c1);
+        k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
+        k_scatter<V, false><<<grid_for(n, kTile, sms * 3), kTileThreads, tile_smem, st>>>(
+            keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
+        uint64_t per64 = (sms * 4ull + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
+        if (per64 > 8) per64 = 8;
+        if (per64 < 1) per64 = 1;
+        const uint32_t per = (uint32_t)per64;
+        k_hist_seg<<<P.D1 * per, kHistThreads, 0, st>>>(keys_out, S.o1, per, L.sigma, L.range, P.gshift, P.D2,
+                                                         S.c2);
+        k_scan<<<1, 1024, 0, st>>>(S.c2, (uint32_t)P.ngroups, S.o2, S.u2);
+        k_scatter<V, true><<<P.D1 * per, kTileThreads, tile_smem, st>>>(
+            keys_out, vals_out, n, S.o1, per, L.sigma, L.range, P.gshift, 0, P.D2, S.u2, S.keys, (V *)S.vals);
+        goff = S.o2;
+        gk = S.keys;
+        gv = (const V *)S.vals;
+    }
+    k_group_sort<V><<<(unsigned)P.ngroups, kGroupThreads, group_smem, st>>>(
+        gk, gv, goff, L.sigma, L.range, P.log2B, L.nb, keys_out, vals_out, bucket_start);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t sort_scratch_bytes(uint64_t n, uint64_t /*m*/, uint32_t vbytes) {
-    return align256(n * 8) + align256(n * vbytes) + 3 * align256((kMaxBins1 + 1) * 4);
+size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes) {
+    const uint64_t nb = m >= kW ? (m - kW + 128) / 64 : 1;   // buckets of >= 64 slots
+    const uint64_t ngroups = (nb + kGroupBuckets - 1) / kGroupBuckets + 1;
+    return align256(n * 8) + align256(n * vbytes) + 3 * align256((kMaxDigits + 1) * 4) +
+           3 * align256((ngroups + 1) * 4);
+}
+
+uint32_t sort_kernel_count(const LayerDesc &L) {
+    const Plan P = make_plan(L);
+    return P.passes == 0 ? 1u : (P.passes == 1 ? 4u : 7u);
 }
 
 cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
                         uint32_t * /*err*/, cudaStream_t st) {
-    if (L.n == 0) {
-        // every bucket empty
-        return cudaMemsetAsync(bucket_start, 0, (size_t)(L.nb + 1) * 4, st);
-    }
+    if (L.n == 0) return cudaMemsetAsync(bucket_start, 0, (size_t)(L.nb + 1) * 4, st);
     switch (vbytes) {
     case 1: return sort_impl<uint8_t>(L, keys, (const uint8_t *)vals, keys_out, (uint8_t *)vals_out,
                                       bucket_start, scratch, st);

@@ -46,7 +46,7 @@ def test_stage_hash_matches_oracle(n, m, layer):
     assert np.array_equal(c.cpu().numpy().view(np.uint64), oc)
 
 
-@pytest.mark.parametrize("n,r", [(300_007, 8), (70_001, 16), (5, 32)])
+@pytest.mark.parametrize("n,r", [(300_007, 8), (70_001, 16), (5, 32), (10_000_019, 8), (3_000_017, 32)])
 def test_stage_sort_groups_by_bucket(n, r):
     seed, layer = 77, 1
     keys, vals = _kv(n, r, seed=n)
