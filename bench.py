@@ -40,7 +40,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="burr", choices=["burr", "reference"])
-    ap.add_argument("--n", type=int, default=100_000_000)
+    ap.add_argument("--keys", type=int, default=100_000_000, help="keys per structure")
     ap.add_argument("--r", type=int, default=8)
     ap.add_argument("--partition-slots", type=int, default=65536)
     ap.add_argument("--cpu-sample", type=int, default=1 << 22, help="keys of the oracle sample")
@@ -193,17 +193,17 @@ def run_reference(a, ws, rank, pg):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(a),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"serial C oracle: build + query of {n_s} keys per step (of the {a.n}-key workload)"},
+                         "sample": f"serial C oracle: build + query of {n_s} keys per step (of the {a.keys}-key workload)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def workload_config(a):
-    return {"workload": f"{a.n} uniform-random 64-bit keys, r={a.r}, w=64, 2-bit thresholds, "
-                        f"partition size {a.partition_slots} slots, plain build + {a.n} queries "
+    return {"workload": f"{a.keys} uniform-random 64-bit keys, r={a.r}, w=64, 2-bit thresholds, "
+                        f"partition size {a.partition_slots} slots, plain build + {a.keys} queries "
                         f"(half members, half non-members)",
-            "n_keys": a.n, "queries": a.n, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
+            "n_keys": a.keys, "queries": a.keys, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
             "partition_slots": a.partition_slots, "load_factor": 1.015, "layers": 4,
             "l2_flush": "inputs larger than L2 (keys 8n bytes)", "parallelism": "one independent structure per GPU"}
 
@@ -222,7 +222,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n, r, P = a.n, a.r, a.partition_slots
+    n, r, P = a.keys, a.r, a.partition_slots
     vb = 1 if r <= 8 else (2 if r <= 16 else 4)
     seed = I.KEY_SEED + rank * 0x100000000        # independent structure per rank
     keys = I.keys_torch(n, dev, seed=seed)
