@@ -49,6 +49,11 @@ def args_():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-steps", action="store_true",
                     help="only run warmup+steps (for ncu launch lists), skip extras")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"],
+                    help="plain: one structure of --keys keys; batched: many independent structures")
+    ap.add_argument("--structures", type=int, default=10_000, help="batched: number of structures")
+    ap.add_argument("--plain-sample", type=int, default=300,
+                    help="batched: structures also built one call each, for the comparison")
     return ap.parse_args()
 
 
@@ -208,11 +213,112 @@ def workload_config(a):
             "l2_flush": "inputs larger than L2 (keys 8n bytes)", "parallelism": "one independent structure per GPU"}
 
 
+def batched_sizes(count: int, seed: int = 2024):
+    """Structure sizes log-uniform in [100, 10^6] keys and value widths uniform
+    in {1, 2, 3, 4, 8} (the many-small-structures workload)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(100), np.log(1_000_000), size=count)).astype(np.int64)
+    rs = rng.choice([1, 2, 3, 4, 8], size=count)
+    return sizes, rs
+
+
+def run_batched(a, ws, rank, local, pg):
+    import numpy as np
+    import torch
+
+    from paper_2411_12365_gb300 import burr
+    from paper_2411_12365_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes, rs = batched_sizes(a.structures, seed=2024 + rank)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    N = int(offs[-1])
+    keys = I.keys_torch(N, dev, seed=I.KEY_SEED + rank * 0x100000000)
+    vals = I.values_torch(keys, 8)
+    params = burr.default_params(partition_slots=0, flags=burr.FLAG_TIMING)
+    chosen = [None]
+
+    def step():
+        hs = burr.build_batch(keys, vals, offs, rs, params=params)
+        chosen[0] = hs[0].export()[64:72]
+        for h in hs:
+            h.free()
+
+    for _ in range(a.warmup):
+        step()
+    # correctness of the timed configuration: a few structures answer their values
+    hs = burr.build_batch(keys, vals, offs, rs, params=params)
+    for s in (0, len(hs) // 2, len(hs) - 1):
+        k = keys[offs[s]:offs[s + 1]]
+        got = hs[s].query(k).to(torch.int64) & ((1 << int(rs[s])) - 1)
+        want = vals[offs[s]:offs[s + 1]].to(torch.int64) & ((1 << int(rs[s])) - 1)
+        assert torch.equal(got, want)
+    P = int(np.frombuffer(hs[0].export()[64:72], dtype=np.uint64)[0])
+    del hs
+    torch.cuda.synchronize()
+    barrier(pg)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(a.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(pg, ev0.elapsed_time(ev1) / a.steps)
+    value = ws * N / (ms / 1e3) / 1e6
+    # equal output, one call per structure: a sample built both ways
+    q = min(a.plain_sample, a.structures)
+    sample = np.random.default_rng(7).choice(a.structures, size=q, replace=False)
+    sub_sizes, sub_rs = sizes[sample], rs[sample]
+    sub_offs = np.concatenate([[0], np.cumsum(sub_sizes)]).astype(np.int64)
+    sub_keys = torch.cat([keys[offs[s]:offs[s + 1]] for s in sample])
+    sub_vals = torch.cat([vals[offs[s]:offs[s + 1]] for s in sample])
+    pp = burr.default_params(partition_slots=P, min_partition_slots=P)
+    t0 = time.perf_counter()
+    hs = burr.build_batch(sub_keys, sub_vals, sub_offs, sub_rs, params=pp)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    ex_batch = [h.export() for h in hs]
+    del hs
+    t0 = time.perf_counter()
+    solo = []
+    for i in range(q):
+        k = sub_keys[sub_offs[i]:sub_offs[i + 1]]
+        v = sub_vals[sub_offs[i]:sub_offs[i + 1]]
+        solo.append(burr.build(k, v, int(sub_rs[i]), params=pp))
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    equal = all(solo[i].export() == ex_batch[i] for i in range(q))
+    n_sub = int(sub_offs[-1])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"batched build of {a.structures} independent structures, sizes log-uniform "
+                                   f"in [100, 10^6] keys, r uniform in {{1,2,3,4,8}}, one launch per stage "
+                                   f"and layer, partition size autotuned",
+                       "structures": a.structures, "total_keys": N, "partition_slots_autotuned": P,
+                       "l2_flush": "inputs larger than L2", "parallelism": "independent structures"},
+            "breakdown": {"sample_structures": q, "sample_keys": n_sub,
+                          "batched_sample_mkeys_s": n_sub / t_batch / 1e6,
+                          "plain_one_call_per_structure_sample_mkeys_s": n_sub / t_plain / 1e6,
+                          "sample_exports_equal": equal},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     ws, rank, local, pg = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank, pg)
+        return
+    if a.workload == "batched":
+        run_batched(a, ws, rank, local, pg)
         return
     import numpy as np
     import torch

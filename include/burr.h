@@ -132,6 +132,31 @@ int burr_build(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
                const burr_params *p, void *stream, burr_handle **out);
 
 /*
+ * Build `count` independent structures together (the many-small-structures use
+ * of retrieval, e.g. inside perfect hashing, Sec. 1 "Applications"): one
+ * launch per stage and layer covers every structure, so thousands of small
+ * builds share the GPU instead of running one after the other.
+ *   keys, values  all structures' keys and values back to back (host or
+ *                 device); structure s owns [offsets[s], offsets[s+1]).
+ *                 Values use the value type of the largest r in the batch.
+ *   offsets       host array of count+1 entries, offsets[0] = 0, non-decreasing.
+ *   r             host array of count value widths (1..32).
+ *   p             parameters shared by all structures (NULL = defaults); with
+ *                 p->partition_slots == 0 the library picks P in {2^14, 2^15,
+ *                 2^16} so that the first layer has at least 8 partitions per
+ *                 SM, and records it in every structure's parameters.
+ *   out           host array of count handles.
+ * Each structure follows exactly the single-structure rules (its export equals
+ * burr_build of its keys with the same parameters, including the chosen P).
+ * Each handle is used and freed like any other; the device tables of the batch
+ * are released with the last of its handles.  A structure must have at most
+ * 64*1024 buckets (about 8.5M keys at the default load); larger ones go
+ * through burr_build.  Bucket size must be 128.
+ */
+int burr_build_batch(const uint64_t *keys, const void *values, const uint64_t *offsets, const uint32_t *r,
+                     uint32_t count, const burr_params *p, void *stream, burr_handle **out);
+
+/*
  * Query n keys (host or device), writing n values of the handle's value type
  * to out (host or device).  Stream-ordered: with device keys and output the
  * call only enqueues work on `stream`; with any host pointer it copies through

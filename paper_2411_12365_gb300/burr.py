@@ -50,7 +50,7 @@ class Stats(C.Structure):
     ]
 
 
-EXPORTED = ["burr_default_params", "burr_build", "burr_query", "burr_size_bytes", "burr_export",
+EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query", "burr_size_bytes", "burr_export",
             "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
             "burr_stage_sort", "burr_stage_sort_noalloc"]
 
@@ -74,6 +74,9 @@ def load(path: str | None = None):
         L.burr_default_params.restype = i
         L.burr_build.argtypes = [p, p, u64, u32, C.POINTER(Params), p, C.POINTER(p)]
         L.burr_build.restype = i
+        L.burr_build_batch.argtypes = [p, p, C.POINTER(u64), C.POINTER(u32), u32, C.POINTER(Params), p,
+                                       C.POINTER(p)]
+        L.burr_build_batch.restype = i
         L.burr_query.argtypes = [p, p, p, u64, p]
         L.burr_query.restype = i
         L.burr_size_bytes.argtypes = [p, C.POINTER(u64)]
@@ -211,6 +214,24 @@ def build(keys, values, r: int, params: Params | None = None, stream=None, **kw)
     out = C.c_void_p()
     _check(load().burr_build(kp, vp, n, r, C.byref(params), st, C.byref(out)))
     return Handle(out.value, r)
+
+
+def build_batch(keys, values, offsets, rs, params: Params | None = None, stream=None, **kw) -> list:
+    """burr_build_batch: structure s owns keys[offsets[s]:offsets[s+1]] with r = rs[s].
+    Returns one Handle per structure."""
+    if params is None:
+        params = default_params(**kw)
+    offsets = [int(x) for x in offsets]
+    rs = [int(x) for x in rs]
+    S = len(rs)
+    assert len(offsets) == S + 1
+    kp, st, _kk = _ptr_and_stream(keys, _stream_value(stream))
+    vp, _, _vk = _ptr_and_stream(values, st)
+    offs = (C.c_uint64 * (S + 1))(*offsets)
+    rr = (C.c_uint32 * S)(*rs)
+    outs = (C.c_void_p * S)()
+    _check(load().burr_build_batch(kp, vp, offs, rr, S, C.byref(params), st, outs))
+    return [Handle(outs[i], rs[i]) for i in range(S)]
 
 
 def stage_hash(keys, seed: int, layer_index: int, m: int, stream=None):

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,16 @@ struct LayerStore {
     uint64_t *z = nullptr;        // (m/64)*r words
 };
 
+// Device tables of a batched build, shared by the handles of its structures
+// and released with the last of them.
+struct BatchStorage {
+    std::vector<void *> ptrs;
+    ~BatchStorage() {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+};
+
 }  // namespace
 
 int burr::set_error(int code, const char *msg) {
@@ -159,11 +170,16 @@ struct burr_handle {
     float stage_ms[BURR_MAX_LAYERS + 1][3] = {};
     float total_ms = 0;
     uint64_t launches = 0;
+    std::shared_ptr<BatchStorage> shared;   // set for a structure of a batched build
 };
 
 namespace {
 
 void free_layers(burr_handle *h) {
+    if (h->shared) {                        // tables belong to the batch
+        for (auto &S : h->L) S.thresh = S.z = nullptr;
+        return;
+    }
     for (auto &S : h->L) {
         if (S.thresh) cudaFree(S.thresh);
         if (S.z) cudaFree(S.z);
@@ -434,6 +450,305 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     return BURR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched build: S independent structures, one launch per stage per layer over
+// all of them.  Each structure follows exactly the single-structure rules
+// (sizes, seeds, cuts, thresholds), so its export equals its solo build with
+// the same parameters; only the work is scheduled together.
+// ---------------------------------------------------------------------------
+
+// Partition size for a batch whose caller left it to the library: the largest
+// of 2^16, 2^15, 2^14 slots that still gives every SM at least 8 partitions in
+// the first layer (more partitions hide more latency; smaller ones bump more
+// keys at the cuts).
+uint64_t autotune_partition_slots(const std::vector<uint64_t> &n, double alpha) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (uint64_t P = 65536; P >= 16384; P /= 2) {
+        uint64_t parts = 0;
+        for (uint64_t x : n) parts += num_partitions(layer_slots(x, alpha), P, P);
+        if (parts >= 8ull * (uint64_t)sms) return P;
+    }
+    return 16384;
+}
+
+struct BatchTables {
+    std::vector<StructDesc> sd;
+    std::vector<uint32_t> part_struct, group_struct, tile_struct;
+    std::vector<uint64_t> tile_lo;
+    std::vector<uint32_t> who;   // active index -> structure index
+    uint64_t nbuckets = 0, ngroups = 0, nparts = 0, slots = 0, tw = 0, zw = 0, nkeys = 0;
+};
+
+// Descriptors of one layer for the structures in `who` with counts n[s].
+// fb_attempt == nullptr: a bumping layer with index l; else the base case.
+int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std::vector<uint64_t> &offsets,
+                 const std::vector<uint64_t> &n, const std::vector<uint32_t> &who, uint32_t l,
+                 const std::vector<uint32_t> *fb_attempt, BatchTables &T) {
+    T = BatchTables();
+    T.who = who;
+    for (uint32_t i = 0; i < who.size(); ++i) {
+        const uint32_t s = who[i];
+        const bool fb = fb_attempt != nullptr;
+        const uint64_t m = fb ? fallback_slots(n[s], p.fallback_slack, (*fb_attempt)[s])
+                              : layer_slots(n[s], p.load_factor);
+        if (m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "structure %u needs >= 2^32 slots", s);
+        const uint64_t K = fb ? 1 : num_partitions(m, p.partition_slots, p.min_partition_slots);
+        const uint64_t sigma = layer_seed(p.seed, fb ? p.layers + (*fb_attempt)[s] : l);
+        StructDesc D;
+        memset(&D, 0, sizeof(D));
+        D.L = make_desc(p, r[s], n[s], m, sigma, K, fb);
+        const uint64_t ng = (D.L.nb + 63) / 64;
+        if (ng > kMaxGroupsPerStruct)
+            return fail(BURR_ERR_INVALID,
+                        "structure %u (%llu keys) is too large for a batched build; build it with burr_build", s,
+                        (unsigned long long)n[s]);
+        D.key_base = offsets[s];
+        D.out_base = offsets[s];
+        D.bucket_base = T.nbuckets;
+        D.group_base = T.ngroups;
+        D.slot_base = T.slots;
+        D.tw_base = T.tw;
+        D.z_base = T.zw;
+        D.part_base = (uint32_t)T.nparts;
+        D.ngroups = (uint32_t)ng;
+        T.sd.push_back(D);
+        for (uint64_t k = 0; k < K; ++k) T.part_struct.push_back(i);
+        for (uint64_t g = 0; g < ng; ++g) T.group_struct.push_back(i);
+        for (uint64_t t = 0; t < n[s]; t += kSortTile) {
+            T.tile_struct.push_back(i);
+            T.tile_lo.push_back(offsets[s] + t);
+        }
+        T.nbuckets += D.L.nb;
+        T.ngroups += ng;
+        T.nparts += K;
+        T.slots += m;
+        T.tw += (D.L.nb + 31) / 32;
+        T.zw += (m / 64) * r[s];
+        T.nkeys += n[s];
+    }
+    return BURR_OK;
+}
+
+// Copy a host vector into a device buffer taken from the arena.
+template <typename X>
+cudaError_t upload(Arena &ar, const std::vector<X> &v, X **d, cudaStream_t st) {
+    cudaError_t e = ar.alloc((void **)d, std::max<size_t>(v.size(), 1) * sizeof(X));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, st);
+}
+
+int build_batch_impl(const uint64_t *keys, const void *values, const std::vector<uint64_t> &offsets,
+                     const std::vector<uint32_t> &r, const burr_params &p, cudaStream_t st,
+                     std::vector<burr_handle *> &hs, const std::shared_ptr<BatchStorage> &store) {
+    const uint32_t S = (uint32_t)r.size();
+    uint32_t rmax = 1;
+    for (uint32_t x : r) rmax = std::max(rmax, x);
+    const uint32_t vb = value_bytes(rmax);
+    const uint64_t N = offsets[S];
+    keep_pool_memory();
+    Arena ar(st);
+    Timer tm((p.flags & BURR_FLAG_TIMING) != 0, st);
+    const int t_begin = tm.mark();
+
+    const uint64_t *dkeys = keys;
+    const void *dvals = values;
+    if (!is_device_ptr(keys)) {
+        void *d;
+        CK(ar.alloc(&d, N * 8), "alloc keys");
+        CK(cudaMemcpyAsync(d, keys, N * 8, cudaMemcpyHostToDevice, st), "copy keys");
+        dkeys = (const uint64_t *)d;
+    }
+    if (!is_device_ptr(values)) {
+        void *d;
+        CK(ar.alloc(&d, N * vb), "alloc values");
+        CK(cudaMemcpyAsync(d, values, N * vb, cudaMemcpyHostToDevice, st), "copy values");
+        dvals = d;
+    }
+    void *bk[2], *bv2[2], *sk, *sv, *ctr;
+    for (int i = 0; i < 2; ++i) {
+        CK(ar.alloc(&bk[i], N * 8), "alloc bumped keys");
+        CK(ar.alloc(&bv2[i], N * vb), "alloc bumped values");
+    }
+    CK(ar.alloc(&sk, N * 8), "alloc sorted keys");
+    CK(ar.alloc(&sv, N * vb), "alloc sorted values");
+    CK(ar.alloc(&ctr, (size_t)S * 12 + 64), "alloc counters");
+    unsigned long long *bcount = (unsigned long long *)ctr;
+    uint32_t *ffail = (uint32_t *)((char *)ctr + (size_t)S * 8);
+    uint32_t *err = ffail + S;
+    // buffers sized by the largest layer seen so far
+    void *scratch = nullptr, *bst = nullptr, *cg = nullptr, *yg = nullptr;
+    uint64_t cap_scratch = 0, cap_nb = 0, cap_slots = 0;
+    auto ensure = [&](const BatchTables &T) -> int {
+        const size_t need = sort_batch_scratch_bytes(T.nkeys, T.ngroups, vb);
+        if (need > cap_scratch) {
+            if (scratch) ar.release(scratch);
+            CK(ar.alloc(&scratch, need), "alloc sort scratch");
+            cap_scratch = need;
+        }
+        if (T.nbuckets + 1 > cap_nb) {
+            if (bst) ar.release(bst);
+            CK(ar.alloc(&bst, (T.nbuckets + 1) * 4), "alloc bucket offsets");
+            cap_nb = T.nbuckets + 1;
+        }
+        if (T.slots > cap_slots) {
+            if (cg) ar.release(cg);
+            if (yg) ar.release(yg);
+            CK(ar.alloc(&cg, T.slots * 8), "alloc band");
+            CK(ar.alloc(&yg, T.slots * vb), "alloc band values");
+            cap_slots = T.slots;
+        }
+        return BURR_OK;
+    };
+    auto view = [&](const BatchTables &T, BatchView &v) -> int {
+        StructDesc *dsd;
+        uint32_t *dps, *dgs, *dts;
+        uint64_t *dtl;
+        CK(upload(ar, T.sd, &dsd, st), "upload descriptors");
+        CK(upload(ar, T.part_struct, &dps, st), "upload partitions");
+        CK(upload(ar, T.group_struct, &dgs, st), "upload groups");
+        CK(upload(ar, T.tile_struct, &dts, st), "upload tiles");
+        CK(upload(ar, T.tile_lo, &dtl, st), "upload tiles");
+        v.sd = dsd;
+        v.part_struct = dps;
+        v.group_struct = dgs;
+        v.tile_struct = dts;
+        v.tile_lo = dtl;
+        v.fail = ffail;
+        v.nstruct = (uint32_t)T.sd.size();
+        v.nparts = (uint32_t)T.nparts;
+        v.ngroups = (uint32_t)T.ngroups;
+        v.ntiles = (uint32_t)T.tile_struct.size();
+        v.nbuckets = T.nbuckets;
+        v.nkeys = T.nkeys;
+        return BURR_OK;
+    };
+    auto table_alloc = [&](size_t bytes, uint64_t **d) -> cudaError_t {
+        *d = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)d, std::max<size_t>(bytes, 8), st);
+        if (e == cudaSuccess) store->ptrs.push_back(*d);
+        return e;
+    };
+
+    std::vector<uint64_t> n(S);
+    for (uint32_t s = 0; s < S; ++s) n[s] = offsets[s + 1] - offsets[s];
+    const LayerDesc none = make_desc(p, 1, 0, 64, 0, 0, false);
+    const uint64_t *cur_k = dkeys;
+    const void *cur_v = dvals;
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        std::vector<uint32_t> who;
+        for (uint32_t s = 0; s < S; ++s) {
+            hs[s]->L[l].n = n[s];
+            hs[s]->L[l].seed_index = l;
+            if (n[s]) who.push_back(s);
+        }
+        if (who.empty()) break;
+        BatchTables T;
+        int rc = batch_tables(p, r, offsets, n, who, l, nullptr, T);
+        if (rc) return rc;
+        if ((rc = ensure(T))) return rc;
+        BatchView v;
+        if ((rc = view(T, v))) return rc;
+        uint64_t *th, *z;
+        CK(table_alloc(T.tw * 8, &th), "alloc thresholds");
+        CK(table_alloc(T.zw * 8, &z), "alloc tables");
+        CK(cudaMemsetAsync(th, 0, std::max<uint64_t>(T.tw, 1) * 8, st), "clear thresholds");
+        CK(cudaMemsetAsync(ctr, 0, (size_t)S * 12 + 64, st), "clear counters");
+        const int w = (int)(l & 1);
+        const int t0 = tm.mark();
+        CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
+        const int t1 = tm.mark();
+        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th,
+                       (uint64_t *)bk[w], bv2[w], bcount, err, st, &v), "band");
+        const int t2 = tm.mark();
+        CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
+        const int t3 = tm.mark();
+        for (auto *h : hs) h->launches += 6;
+        std::vector<unsigned long long> cnt(who.size());
+        uint32_t e = 0;
+        CK(cudaMemcpyAsync(cnt.data(), bcount, cnt.size() * 8, cudaMemcpyDeviceToHost, st), "read counters");
+        CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
+        CK(cudaStreamSynchronize(st), "layer");
+        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the 512-slot window", l);
+        if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
+        for (uint32_t i = 0; i < who.size(); ++i) {
+            const uint32_t s = who[i];
+            const StructDesc &D = T.sd[i];
+            LayerStore &Ls = hs[s]->L[l];
+            Ls.m = D.L.m;
+            Ls.nb = D.L.nb;
+            Ls.K = D.L.K;
+            Ls.sigma = D.L.sigma;
+            Ls.nbumped = cnt[i];
+            Ls.thresh = th + D.tw_base;
+            Ls.z = z + D.z_base;
+            hs[s]->stage_ms[l][0] = tm.ms(t0, t1);
+            hs[s]->stage_ms[l][1] = tm.ms(t1, t2);
+            hs[s]->stage_ms[l][2] = tm.ms(t2, t3);
+            n[s] = cnt[i];
+        }
+        cur_k = (const uint64_t *)bk[w];
+        cur_v = bv2[w];
+    }
+    // base case of every structure with keys left; retries per structure
+    std::vector<uint32_t> attempt(S, 0), pending;
+    for (uint32_t s = 0; s < S; ++s) {
+        hs[s]->L[p.layers].n = n[s];
+        hs[s]->L[p.layers].seed_index = p.layers;
+        if (n[s]) pending.push_back(s);
+    }
+    const int wfb = (int)(p.layers & 1);
+    while (!pending.empty()) {
+        BatchTables T;
+        int rc = batch_tables(p, r, offsets, n, pending, p.layers, &attempt, T);
+        if (rc) return rc;
+        if ((rc = ensure(T))) return rc;
+        BatchView v;
+        if ((rc = view(T, v))) return rc;
+        uint64_t *z;
+        CK(table_alloc(T.zw * 8, &z), "alloc tables");
+        CK(cudaMemsetAsync(ctr, 0, (size_t)S * 12 + 64, st), "clear counters");
+        CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
+        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr,
+                       (uint64_t *)bk[wfb], bv2[wfb], bcount, err, st, &v), "band");
+        CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
+        for (auto *h : hs) h->launches += 6;
+        std::vector<uint32_t> f(pending.size());
+        uint32_t e = 0;
+        CK(cudaMemcpyAsync(f.data(), ffail, f.size() * 4, cudaMemcpyDeviceToHost, st), "read flags");
+        CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
+        CK(cudaStreamSynchronize(st), "base case");
+        if (e) return fail(BURR_ERR_INTERNAL, "base case: device error 0x%x", e);
+        std::vector<uint32_t> again;
+        for (uint32_t i = 0; i < pending.size(); ++i) {
+            const uint32_t s = pending[i];
+            const StructDesc &D = T.sd[i];
+            if (f[i] & kErrUnsolvable) {
+                if (++attempt[s] > p.fallback_max_retries)
+                    return fail(BURR_ERR_UNSOLVABLE, "structure %u: base case unsolved after %u retries", s,
+                                p.fallback_max_retries);
+                again.push_back(s);
+                continue;
+            }
+            LayerStore &F = hs[s]->L[p.layers];
+            F.m = D.L.m;
+            F.nb = D.L.nb;
+            F.K = 1;
+            F.sigma = D.L.sigma;
+            F.seed_index = p.layers + attempt[s];
+            F.z = z + D.z_base;
+            hs[s]->fb_attempt = attempt[s];
+        }
+        pending.swap(again);
+    }
+    const int t_end = tm.mark();
+    CK(cudaStreamSynchronize(st), "build");
+    const float total = tm.ms(t_begin, t_end);
+    for (auto *h : hs) h->total_ms = total;
+    return BURR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -487,6 +802,62 @@ int burr_build(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         }
     }
     *out = h;
+    return BURR_OK;
+}
+
+int burr_build_batch(const uint64_t *keys, const void *values, const uint64_t *offsets, const uint32_t *r,
+                     uint32_t count, const burr_params *pin, void *stream, burr_handle **out) {
+    if (!out || !offsets || !r || count == 0) return fail(BURR_ERR_INVALID, "NULL argument or empty batch");
+    for (uint32_t s = 0; s < count; ++s) out[s] = nullptr;
+    burr_params p;
+    if (pin) p = *pin;
+    else burr_default_params(&p);
+    if (p.bucket_slots != 128) return fail(BURR_ERR_INVALID, "batched builds use bucket_slots = 128");
+    std::vector<uint64_t> offs(offsets, offsets + count + 1);
+    std::vector<uint32_t> rs(r, r + count);
+    if (offs[0] != 0) return fail(BURR_ERR_INVALID, "offsets[0] must be 0");
+    std::vector<uint64_t> n(count);
+    for (uint32_t s = 0; s < count; ++s) {
+        if (offs[s + 1] < offs[s]) return fail(BURR_ERR_INVALID, "offsets must not decrease");
+        n[s] = offs[s + 1] - offs[s];
+    }
+    if (offs[count] >= (1ull << 32)) return fail(BURR_ERR_INVALID, "total keys >= 2^32");
+    if (offs[count] > 0 && (!keys || !values)) return fail(BURR_ERR_INVALID, "keys/values are NULL");
+    if (p.partition_slots == 0) {
+        p.partition_slots = autotune_partition_slots(n, p.load_factor > 0 ? p.load_factor : 1.0);
+        p.min_partition_slots = p.partition_slots;
+    }
+    for (uint32_t s = 0; s < count; ++s) {
+        const int rc = validate(p, rs[s]);
+        if (rc) return rc;
+    }
+    auto store = std::make_shared<BatchStorage>();
+    std::vector<burr_handle *> hs(count);
+    for (uint32_t s = 0; s < count; ++s) {
+        hs[s] = new (std::nothrow) burr_handle();
+        if (!hs[s]) {
+            for (uint32_t q = 0; q < s; ++q) delete hs[q];
+            return fail(BURR_ERR_OOM, "host allocation");
+        }
+        hs[s]->p = p;
+        hs[s]->r = rs[s];
+        hs[s]->vbytes = value_bytes(rs[s]);
+        hs[s]->n = n[s];
+        hs[s]->shared = store;
+        for (uint32_t l = 0; l <= p.layers; ++l) hs[s]->L[l].seed_index = l;
+    }
+    int rc = BURR_OK;
+    if (offs[count] > 0) {
+        // values are passed in the value type of the widest r; per-structure
+        // value types apply to queries (the handle's r)
+        rc = build_batch_impl(keys, values, offs, rs, p, (cudaStream_t)stream, hs, store);
+    }
+    if (rc) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        for (auto *h : hs) delete h;
+        return rc;
+    }
+    for (uint32_t s = 0; s < count; ++s) out[s] = hs[s];
     return BURR_OK;
 }
 

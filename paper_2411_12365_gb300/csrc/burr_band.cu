@@ -77,6 +77,18 @@ struct BandArgs {
     V *bvals;
     unsigned long long *bcount;
     uint32_t *err;
+    BatchView bv;            // sd == nullptr: a single layer described by L
+};
+
+// What one warp works on: a partition of one structure's layer, and where that
+// structure's data sits in the layer-wide arrays (all bases 0 for a single
+// structure).
+struct Ctx {
+    LayerDesc L;
+    uint64_t part;
+    uint64_t bucket_base, slot_base, tw_base, out_base;
+    unsigned long long *bcount;
+    uint32_t *fail;          // base case, batched: per-structure flag
 };
 
 enum { kOk = 0, kDependent = 1, kOverflow = 2 };
@@ -95,9 +107,9 @@ __device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int 
 // bB: equations in ascending offset order; S.first[o] = first index with
 // offset >= o.
 template <typename V>
-__device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, uint32_t base, uint32_t cnt, uint32_t bB,
-                           int lane) {
-    const LayerDesc &L = a.L;
+__device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t base, uint32_t cnt,
+                           uint32_t bB, int lane) {
+    const LayerDesc &L = x.L;
     for (int i = lane; i < 132; i += 32) S.first[i] = 0;
     __syncwarp();
     uint64_t c[kStagePerLane];
@@ -227,14 +239,14 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 // Insert the rows of bucket [rs, re) whose offset lies in [olo, ohi) as one
 // set; on a dependency or overflow every row this call stored is removed.
 template <typename V>
-__device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, uint32_t rs, uint32_t re, uint32_t bB,
-                          uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
+__device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
+                          uint32_t bB, uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
     if (lane == 0) S.ncommit = 0;
     __syncwarp();
     for (uint32_t base = rs; base < re; base += kStage) {
         const uint32_t cnt = min((uint32_t)kStage, re - base);
         if (staged_base != base) {
-            stage_rows(S, a, base, cnt, bB, lane);
+            stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
         const int rc = stream_insert(S, S.first[olo], S.first[ohi], bB, lane);
@@ -249,8 +261,8 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, uint32_t rs, ui
 
 // Rows of the bucket below threshold t leave for the next layer.
 template <typename V>
-__device__ void emit_bumped(const BandArgs<V> &a, uint32_t rs, uint32_t re, uint32_t bB, uint32_t t,
-                            int lane) {
+__device__ void emit_bumped(const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re, uint32_t bB,
+                            uint32_t t, int lane) {
     for (uint32_t base = rs; base < re; base += 32) {
         const uint32_t idx = base + lane;
         bool bump = false;
@@ -258,16 +270,16 @@ __device__ void emit_bumped(const BandArgs<V> &a, uint32_t rs, uint32_t re, uint
         V val = 0;
         if (idx < re) {
             key = a.keys[idx];
-            bump = (start_slot(key, a.L.sigma, a.L.range) - bB) < t;
+            bump = (start_slot(key, x.L.sigma, x.L.range) - bB) < t;
             if (bump) val = a.vals[idx];
         }
         const uint32_t mask = __ballot_sync(kFull, bump);
         if (!mask) continue;
         unsigned long long ob = 0;
-        if (lane == 0) ob = atomicAdd(a.bcount, (unsigned long long)__popc(mask));
+        if (lane == 0) ob = atomicAdd(x.bcount, (unsigned long long)__popc(mask));
         ob = __shfl_sync(kFull, ob, 0);
         if (bump) {
-            const unsigned long long o = ob + __popc(mask & ((1u << lane) - 1u));
+            const unsigned long long o = x.out_base + ob + __popc(mask & ((1u << lane) - 1u));
             a.bkeys[o] = key;
             a.bvals[o] = val;
         }
@@ -276,13 +288,13 @@ __device__ void emit_bumped(const BandArgs<V> &a, uint32_t rs, uint32_t re, uint
 
 // Write ring slots [from, to) to the global band and clear them.
 template <typename V>
-__device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, uint64_t from, uint64_t to,
-                                      int lane) {
+__device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint64_t from,
+                                      uint64_t to, int lane) {
     __syncwarp();
     for (uint64_t s = from + lane; s < to; s += 32) {
         const uint32_t ri = (uint32_t)s & kRingMask;
-        a.Cg[s] = S.ring[ri].c;
-        a.Yg[s] = (V)(S.ring[ri].y & 0xffffffffull);
+        a.Cg[x.slot_base + s] = S.ring[ri].c;
+        a.Yg[x.slot_base + s] = (V)(S.ring[ri].y & 0xffffffffull);
         S.ring[ri].c = 0;
         S.ring[ri].y = 0;
     }
@@ -293,9 +305,30 @@ template <typename V>
 __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const LayerDesc &L = a.L;
-    const uint64_t part = (uint64_t)blockIdx.x * kBandWarps + warp;
-    if (part >= L.K) return;
+    const uint64_t gp = (uint64_t)blockIdx.x * kBandWarps + warp;
+    Ctx x;
+    if (a.bv.sd) {
+        if (gp >= a.bv.nparts) return;
+        const uint32_t si = a.bv.part_struct[gp];
+        const StructDesc &D = a.bv.sd[si];
+        x.L = D.L;
+        x.part = gp - D.part_base;
+        x.bucket_base = D.bucket_base;
+        x.slot_base = D.slot_base;
+        x.tw_base = D.tw_base;
+        x.out_base = D.out_base;
+        x.bcount = a.bcount + si;
+        x.fail = a.bv.fail ? a.bv.fail + si : nullptr;
+    } else {
+        if (gp >= a.L.K) return;
+        x.L = a.L;
+        x.part = gp;
+        x.bucket_base = x.slot_base = x.tw_base = x.out_base = 0;
+        x.bcount = a.bcount;
+        x.fail = nullptr;
+    }
+    const LayerDesc &L = x.L;
+    const uint64_t part = x.part;
     BandWarpSmem &S = smem[warp];
 
     const uint64_t b0 = part * L.P / L.B;
@@ -320,27 +353,27 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     for (uint64_t b = b0; b < b1; ++b) {
         const uint64_t bB = b * L.B;
         if (bB > flushed) {
-            flush(S, a, flushed, bB, lane);
+            flush(S, a, x, flushed, bB, lane);
             flushed = bB;
         }
         const bool cut = (part > 0 && b == b0 && !L.fallback);
         const uint32_t forced = cut ? flevel : 0;
         uint32_t code = cut ? fcode : 0;
-        const uint32_t rs = a.bstart[b], re = a.bstart[b + 1];
+        const uint32_t rs = a.bstart[x.bucket_base + b], re = a.bstart[x.bucket_base + b + 1];
         if (re > rs) {
             uint32_t staged = 0xffffffffu;
-            int rc = insert_set(S, a, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
+            int rc = insert_set(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
             if (rc == kOverflow) return;
             if (rc == kDependent) {
                 if (L.fallback) {
-                    if (lane == 0) atomicOr(a.err, kErrUnsolvable);
+                    if (lane == 0) atomicOr(x.fail ? x.fail : a.err, kErrUnsolvable);
                     return;
                 }
                 code = 3;
                 for (int k = 2; k >= 0; --k) {
                     if (lv[k + 1] <= forced) break;
                     const uint32_t lo = max(lv[k], forced), hi = lv[k + 1];
-                    const int rc2 = insert_set(S, a, rs, re, (uint32_t)bB, lo, hi, staged, lane);
+                    const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lo, hi, staged, lane);
                     if (rc2 == kOverflow) return;
                     if (rc2 == kDependent) {
                         code = (uint32_t)k + 1;
@@ -350,11 +383,12 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                 }
             }
             const uint32_t t = lv[code];
-            if (!L.fallback && t > 0) emit_bumped(a, rs, re, (uint32_t)bB, t, lane);
+            if (!L.fallback && t > 0) emit_bumped(a, x, rs, re, (uint32_t)bB, t, lane);
         }
         if (!L.fallback) {
             if ((b >> 5) != twi) {
-                if (lane == 0 && tword) atomicOr((unsigned long long *)&a.thresh[twi], (unsigned long long)tword);
+                if (lane == 0 && tword)
+                    atomicOr((unsigned long long *)&a.thresh[x.tw_base + twi], (unsigned long long)tword);
                 tword = 0;
                 twi = b >> 5;
             }
@@ -362,8 +396,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         }
     }
     if (!L.fallback && lane == 0 && tword)
-        atomicOr((unsigned long long *)&a.thresh[twi], (unsigned long long)tword);
-    flush(S, a, flushed, own_hi, lane);
+        atomicOr((unsigned long long *)&a.thresh[x.tw_base + twi], (unsigned long long)tword);
+    flush(S, a, x, flushed, own_hi, lane);
 }
 
 // Back-substitution, right to left over the partition's owned slots, one
@@ -389,11 +423,29 @@ __device__ __forceinline__ uint32_t parity64(uint64_t x) {
 
 template <typename V>
 __global__ void __launch_bounds__(32 * kBsWarps)
-k_backsub(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z) {
+k_backsub(LayerDesc L0, const uint64_t *__restrict__ Cg0, const V *__restrict__ Yg0, uint64_t *__restrict__ Z0,
+          BatchView bv) {
     __shared__ uint64_t sc[kBsWarps][64];
     __shared__ uint32_t sy[kBsWarps][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t part = (uint64_t)blockIdx.x * kBsWarps + warp;
+    const uint64_t gp = (uint64_t)blockIdx.x * kBsWarps + warp;
+    LayerDesc L;
+    uint64_t part;
+    const uint64_t *Cg = Cg0;
+    const V *Yg = Yg0;
+    uint64_t *Z = Z0;
+    if (bv.sd) {
+        if (gp >= bv.nparts) return;
+        const StructDesc &D = bv.sd[bv.part_struct[gp]];
+        L = D.L;
+        part = gp - D.part_base;
+        Cg += D.slot_base;
+        Yg += D.slot_base;
+        Z += D.z_base;
+    } else {
+        L = L0;
+        part = gp;
+    }
     if (part >= L.K) return;
     const uint64_t own_lo = part == 0 ? 0 : part * L.P + kW;
     const uint64_t own_hi = part == L.K - 1 ? L.m : (part + 1) * L.P + kW;
@@ -441,8 +493,9 @@ k_backsub(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg
 template <typename V>
 cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, const uint32_t *bstart,
                       uint64_t *Cg, V *Yg, uint64_t *thresh, uint64_t *bkeys, V *bvals,
-                      unsigned long long *bcount, uint32_t *err, cudaStream_t st) {
+                      unsigned long long *bcount, uint32_t *err, cudaStream_t st, const BatchView *bv) {
     BandArgs<V> a;
+    if (bv) a.bv = *bv;
     a.L = L;
     a.keys = keys;
     a.vals = vals;
@@ -454,7 +507,8 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
     a.bvals = bvals;
     a.bcount = bcount;
     a.err = err;
-    const unsigned grid = (unsigned)((L.K + kBandWarps - 1) / kBandWarps);
+    const uint64_t parts = bv ? bv->nparts : L.K;
+    const unsigned grid = (unsigned)((parts + kBandWarps - 1) / kBandWarps);
     k_band<V><<<grid, 32 * kBandWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -464,29 +518,31 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
 cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh,
                         uint64_t *bumped_keys, void *bumped_vals, unsigned long long *bumped_count,
-                        uint32_t *err, cudaStream_t st) {
-    if (L.K == 0) return cudaSuccess;
+                        uint32_t *err, cudaStream_t st, const BatchView *bv) {
+    if (bv ? bv->nparts == 0 : L.K == 0) return cudaSuccess;
     switch (vbytes) {
     case 1:
         return band_impl<uint8_t>(L, keys, (const uint8_t *)vals, bucket_start, Cg, (uint8_t *)Yg, thresh,
-                                  bumped_keys, (uint8_t *)bumped_vals, bumped_count, err, st);
+                                  bumped_keys, (uint8_t *)bumped_vals, bumped_count, err, st, bv);
     case 2:
         return band_impl<uint16_t>(L, keys, (const uint16_t *)vals, bucket_start, Cg, (uint16_t *)Yg, thresh,
-                                   bumped_keys, (uint16_t *)bumped_vals, bumped_count, err, st);
+                                   bumped_keys, (uint16_t *)bumped_vals, bumped_count, err, st, bv);
     default:
         return band_impl<uint32_t>(L, keys, (const uint32_t *)vals, bucket_start, Cg, (uint32_t *)Yg, thresh,
-                                   bumped_keys, (uint32_t *)bumped_vals, bumped_count, err, st);
+                                   bumped_keys, (uint32_t *)bumped_vals, bumped_count, err, st, bv);
     }
 }
 
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
-                           uint64_t *Z, cudaStream_t st) {
-    if (L.K == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((L.K + kBsWarps - 1) / kBsWarps);
+                           uint64_t *Z, cudaStream_t st, const BatchView *bv) {
+    const uint64_t parts = bv ? bv->nparts : L.K;
+    if (parts == 0) return cudaSuccess;
+    const BatchView v = bv ? *bv : BatchView();
+    const unsigned grid = (unsigned)((parts + kBsWarps - 1) / kBsWarps);
     switch (vbytes) {
-    case 1: k_backsub<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z); break;
-    case 2: k_backsub<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z); break;
-    default: k_backsub<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z); break;
+    case 1: k_backsub<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, v); break;
+    case 2: k_backsub<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, v); break;
+    default: k_backsub<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, v); break;
     }
     return cudaGetLastError();
 }

@@ -58,6 +58,34 @@ struct LayerDesc {
     uint32_t vmask;      // (1 << r) - 1
 };
 
+// One structure's layer inside a batched build: its layer descriptor and
+// where its data sits in the layer-wide arrays shared by the batch.
+struct StructDesc {
+    LayerDesc L;            // the structure's layer (K partitions of P slots)
+    uint64_t key_base;      // its keys in the layer's input buffer: [key_base, key_base + L.n)
+    uint64_t out_base;      // its bumped keys in the next layer's buffer start here
+    uint64_t bucket_base;   // first global bucket (index into the bucket offsets)
+    uint64_t group_base;    // first global sort group (64 buckets)
+    uint64_t slot_base;     // first slot in the layer-wide band arrays
+    uint64_t tw_base;       // first threshold word
+    uint64_t z_base;        // first table word
+    uint32_t part_base;     // first global partition (band and back-substitution)
+    uint32_t ngroups;       // sort groups of the structure
+};
+
+// Device tables of a batched layer (all device pointers).
+struct BatchView {
+    const StructDesc *sd = nullptr;     // per structure
+    const uint32_t *part_struct = nullptr;  // global partition -> structure
+    const uint32_t *group_struct = nullptr; // global sort group -> structure
+    const uint32_t *tile_struct = nullptr;  // sort tile -> structure
+    const uint64_t *tile_lo = nullptr;      // sort tile -> first key index
+    uint32_t *fail = nullptr;               // per structure: base case dependent
+    uint32_t nstruct = 0, nparts = 0, ngroups = 0, ntiles = 0;
+    uint64_t nbuckets = 0;                  // global buckets
+    uint64_t nkeys = 0;                     // keys of the layer (sum over structures)
+};
+
 // Scratch bytes of launch_sort for n keys in a layer of m slots.
 size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes);
 // Kernels one launch_sort of this layer enqueues (n > 0).
@@ -70,14 +98,24 @@ cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
                         uint32_t *err, cudaStream_t st);
 
 // Band + bump (or base case), writing the band of every partition to Cg/Yg.
+// With a batch view (bv != nullptr) L is ignored: every partition of every
+// structure of the view is processed, bumped_count is per structure.
 cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh,
                         uint64_t *bumped_keys, void *bumped_vals, unsigned long long *bumped_count,
-                        uint32_t *err, cudaStream_t st);
+                        uint32_t *err, cudaStream_t st, const BatchView *bv = nullptr);
 
 // Back-substitution of every partition: Z from the band.
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
-                           uint64_t *Z, cudaStream_t st);
+                           uint64_t *Z, cudaStream_t st, const BatchView *bv = nullptr);
+
+// Batched sort: every structure's keys of the layer grouped by global bucket.
+size_t sort_batch_scratch_bytes(uint64_t nkeys, uint64_t ngroups, uint32_t vbytes);
+cudaError_t launch_sort_batch(const BatchView &bv, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                              uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
+                              cudaStream_t st);
+constexpr uint32_t kSortTile = 4096;      // keys per tile of the batched sort
+constexpr uint32_t kMaxGroupsPerStruct = 1024;
 
 // Query descriptor: every layer of a handle.
 struct QueryDesc {

@@ -399,6 +399,163 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched layers: many structures at once.  Every structure's keys sit in its
+// own range of the input buffer; global sort groups and global buckets are
+// numbered structure by structure, so grouping by global group keeps each
+// structure's keys contiguous and in bucket order.  One pass suffices per
+// structure (at most kMaxGroupsPerStruct groups each): tiles never straddle
+// structures (tile tables are built on the host).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kHistThreads)
+k_hist_batch(const uint64_t *__restrict__ keys, BatchView bv, uint32_t gshift, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t sh[kMaxDigits];
+    const uint32_t t = blockIdx.x;
+    const StructDesc &D = bv.sd[bv.tile_struct[t]];
+    const uint64_t lo = bv.tile_lo[t];
+    const uint64_t hi = min(lo + (uint64_t)kSortTile, D.key_base + D.L.n);
+    const uint32_t G = D.ngroups;
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&sh[group_of(keys[i], D.L.sigma, D.L.range, gshift)], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x)
+        if (sh[i]) atomicAdd(&counts[D.group_base + i], sh[i]);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kTileThreads)
+k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, BatchView bv, uint32_t gshift,
+                uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out, V *__restrict__ vals_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
+    V *sval = reinterpret_cast<V *>(skey + kTile);
+    uint16_t *sdig = reinterpret_cast<uint16_t *>(sval + kTile);
+    __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
+    const uint32_t t = blockIdx.x;
+    const StructDesc &D = bv.sd[bv.tile_struct[t]];
+    const uint64_t base = bv.tile_lo[t];
+    const uint32_t cnt = (uint32_t)min((uint64_t)kSortTile, D.key_base + D.L.n - base);
+    const uint32_t G = D.ngroups;
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    uint64_t key[kTileItems];
+    V val[kTileItems];
+    uint32_t dig[kTileItems], rank[kTileItems];
+#pragma unroll
+    for (int j = 0; j < kTileItems; ++j) {
+        const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
+        if (i < cnt) {
+            key[j] = keys[base + i];
+            val[j] = vals[base + i];
+            dig[j] = group_of(key[j], D.L.sigma, D.L.range, gshift);
+            rank[j] = atomicAdd(&hist[dig[j]], 1u);
+        }
+    }
+    __syncthreads();
+    block_scan(hist, excl, G, warp_sums);
+    for (uint32_t d = threadIdx.x; d < G; d += blockDim.x)
+        if (hist[d]) gbase[d] = atomicAdd(&cursor[D.group_base + d], hist[d]);
+#pragma unroll
+    for (int j = 0; j < kTileItems; ++j) {
+        const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
+        if (i < cnt) {
+            const uint32_t p = excl[dig[j]] + rank[j];
+            skey[p] = key[j];
+            sval[p] = val[j];
+            sdig[p] = (uint16_t)dig[j];
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t d = sdig[i];
+        const uint32_t dst = gbase[d] + (i - excl[d]);
+        keys_out[dst] = skey[i];
+        vals_out[dst] = sval[i];
+    }
+}
+
+// One block per global group: as k_group_sort, with the group's structure
+// looked up in the batch tables.
+template <typename V>
+__global__ void __launch_bounds__(kGroupThreads)
+k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, const uint32_t *__restrict__ goff,
+                   BatchView bv, uint32_t log2B, uint64_t *__restrict__ keys_out, V *__restrict__ vals_out,
+                   uint32_t *__restrict__ bucket_start) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
+    V *sval = reinterpret_cast<V *>(skey + kGroupCap);
+    __shared__ uint32_t cnt[kGroupBuckets], cur[kGroupBuckets], warp_sums[32];
+    const uint64_t g = blockIdx.x;
+    const StructDesc &D = bv.sd[bv.group_struct[g]];
+    const uint64_t lg = g - D.group_base;
+    const uint64_t b_lo = lg << kGroupShift;            // first local bucket of the group
+    const uint32_t nbk = (uint32_t)min((uint64_t)kGroupBuckets, D.L.nb - b_lo);
+    const uint64_t sigma = D.L.sigma, range = D.L.range;
+    const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
+    if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    __syncthreads();
+    block_scan(cnt, cur, kGroupBuckets, warp_sums);
+    if (threadIdx.x < nbk) bucket_start[D.bucket_base + b_lo + threadIdx.x] = lo + cur[threadIdx.x];
+    if (g == gridDim.x - 1 && threadIdx.x == 0) bucket_start[bv.nbuckets] = hi;
+    __syncthreads();
+    if (n <= kGroupCap) {
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const uint64_t key = keys[i];
+            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t p = atomicAdd(&cur[b], 1u);
+            skey[p] = key;
+            sval[p] = vals[i];
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            keys_out[lo + i] = skey[i];
+            vals_out[lo + i] = sval[i];
+        }
+    } else {
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const uint64_t key = keys[i];
+            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t p = lo + atomicAdd(&cur[b], 1u);
+            keys_out[p] = key;
+            vals_out[p] = vals[i];
+        }
+    }
+}
+
+template <typename V>
+cudaError_t sort_batch_impl(const BatchView &bv, const uint64_t *keys, const V *vals, uint64_t *keys_out,
+                            V *vals_out, uint32_t *bucket_start, void *scratch, cudaStream_t st) {
+    const uint32_t log2B = 7;   // bucket_slots = 128 for batched builds
+    const uint32_t gshift = log2B + kGroupShift;
+    char *p = (char *)scratch;
+    uint64_t *tk = (uint64_t *)p;   p += align256(bv.nkeys * 8);
+    V *tv = (V *)p;                 p += align256(bv.nkeys * sizeof(V));
+    uint32_t *counts = (uint32_t *)p; p += align256(((uint64_t)bv.ngroups + 1) * 4);
+    uint32_t *goff = (uint32_t *)p;   p += align256(((uint64_t)bv.ngroups + 1) * 4);
+    uint32_t *cursor = (uint32_t *)p;
+    const size_t tile_smem = (size_t)kTile * (8 + sizeof(V) + 2);
+    const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_scatter_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_group_sort_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counts, 0, (size_t)bv.ngroups * 4, st);
+    if (e != cudaSuccess) return e;
+    k_hist_batch<<<bv.ntiles, kHistThreads, 0, st>>>(keys, bv, gshift, counts);
+    k_scan<<<1, 1024, 0, st>>>(counts, bv.ngroups, goff, cursor);
+    k_scatter_batch<V><<<bv.ntiles, kTileThreads, tile_smem, st>>>(keys, vals, bv, gshift, cursor, tk, tv);
+    k_group_sort_batch<V><<<bv.ngroups, kGroupThreads, group_smem, st>>>(tk, tv, goff, bv, log2B, keys_out,
+                                                                          vals_out, bucket_start);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes) {
@@ -406,6 +563,24 @@ size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes) {
     const uint64_t ngroups = (nb + kGroupBuckets - 1) / kGroupBuckets + 1;
     return align256(n * 8) + align256(n * vbytes) + 3 * align256((kMaxDigits + 1) * 4) +
            3 * align256((ngroups + 1) * 4);
+}
+
+size_t sort_batch_scratch_bytes(uint64_t nkeys, uint64_t ngroups, uint32_t vbytes) {
+    return align256(nkeys * 8) + align256(nkeys * vbytes) + 3 * align256((ngroups + 1) * 4);
+}
+
+cudaError_t launch_sort_batch(const BatchView &bv, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                              uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
+                              cudaStream_t st) {
+    if (bv.nkeys == 0 || bv.ngroups == 0) return cudaSuccess;
+    switch (vbytes) {
+    case 1: return sort_batch_impl<uint8_t>(bv, keys, (const uint8_t *)vals, keys_out, (uint8_t *)vals_out,
+                                            bucket_start, scratch, st);
+    case 2: return sort_batch_impl<uint16_t>(bv, keys, (const uint16_t *)vals, keys_out, (uint16_t *)vals_out,
+                                             bucket_start, scratch, st);
+    default: return sort_batch_impl<uint32_t>(bv, keys, (const uint32_t *)vals, keys_out, (uint32_t *)vals_out,
+                                              bucket_start, scratch, st);
+    }
 }
 
 uint32_t sort_kernel_count(const LayerDesc &L) {

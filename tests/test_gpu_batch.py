@@ -1,0 +1,98 @@
+"""Batched build (many independent structures in one pass of launches).
+
+Each structure of a batch follows the single-structure rules, so its export
+must equal burr_build of the same keys with the same parameters (and that one
+equals the serial CPU oracle); queries of each structure return its values.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_12365_gb300 import inputs as I
+from tests.export_format import describe_difference
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_12365_gb300 import burr  # noqa: E402
+
+
+def _batch_inputs(sizes, rs, seed=7):
+    keys = I.keys_torch(int(sum(sizes)), "cuda", seed=seed)
+    vals = I.values_torch(keys, max(rs))
+    # each structure's values masked to its own width
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return keys, vals, offs
+
+
+def _check_batch(sizes, rs, **params):
+    keys, vals, offs = _batch_inputs(sizes, rs)
+    hs = burr.build_batch(keys, vals, offs, rs, **params)
+    P = hs[0].export()[56:64] if False else None  # noqa: F841
+    for s, h in enumerate(hs):
+        a, b = int(offs[s]), int(offs[s + 1])
+        k, v = keys[a:b], vals[a:b]
+        p = burr.default_params(**params)
+        ex = h.export()
+        if params.get("partition_slots", 1) == 0:
+            # the chosen P is recorded in the export header (u64 after seed, alpha bits, n)
+            chosen = int(np.frombuffer(ex[64:72], dtype=np.uint64)[0])
+            p = burr.default_params(**{**params, "partition_slots": chosen, "min_partition_slots": chosen})
+        vt = burr.value_torch_dtype(rs[s])
+        vs = (v.to(torch.int64) & ((1 << rs[s]) - 1)).to(vt) if vt != vals.dtype or rs[s] < 8 else v
+        solo = burr.build(k, vs, rs[s], params=p).export()
+        assert ex == solo, f"structure {s}: {describe_difference(ex, solo)}"
+        if b > a:
+            got = h.query(k).cpu().numpy().astype(np.int64) & ((1 << rs[s]) - 1)
+            want = vs.cpu().numpy().astype(np.int64) & ((1 << rs[s]) - 1)
+            assert np.array_equal(got, want)
+    return hs, keys, vals, offs
+
+
+def test_batch_small_mixed():
+    rng = np.random.default_rng(1)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(100), np.log(30000), size=40))]
+    sizes[3] = 0                       # an empty structure
+    sizes[7] = 1
+    rs = [int(x) for x in rng.choice([1, 2, 3, 4, 8], size=len(sizes))]
+    _check_batch(sizes, rs, partition_slots=4096, min_partition_slots=4096)
+
+
+def test_batch_matches_oracle():
+    sizes = [5000, 123, 70000, 2]
+    rs = [8, 3, 1, 4]
+    hs, keys, vals, offs = _check_batch(sizes, rs, partition_slots=2048, min_partition_slots=2048)
+    k_np = keys.cpu().numpy().view(np.uint64)
+    v_np = vals.cpu().numpy().astype(np.uint32)
+    for s in range(len(sizes)):
+        a, b = int(offs[s]), int(offs[s + 1])
+        ref = O.build(k_np[a:b], v_np[a:b] & ((1 << rs[s]) - 1), r=rs[s], partition_slots=2048,
+                      min_partition_slots=2048)
+        assert ref.ok and hs[s].export() == ref.export(), s
+
+
+def test_batch_autotuned_partition_size_and_large_structures():
+    rng = np.random.default_rng(2)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(1000), np.log(600000), size=12))]
+    rs = [8] * len(sizes)
+    hs, *_ = _check_batch(sizes, rs, partition_slots=0)
+    chosen = {int(np.frombuffer(h.export()[64:72], dtype=np.uint64)[0]) for h in hs}
+    assert len(chosen) == 1 and chosen.pop() in (16384, 32768, 65536)
+
+
+def test_batch_base_case_heavy():
+    # few bumping layers: every structure ends in the base case, some retry
+    sizes = [3000, 40, 500, 12000]
+    rs = [8, 8, 2, 8]
+    _check_batch(sizes, rs, layers=1, partition_slots=1024, min_partition_slots=1024)
+
+
+def test_batch_rejects_too_large_structure():
+    keys = I.keys_torch(9_000_000, "cuda")
+    vals = I.values_torch(keys, 8)
+    with pytest.raises(burr.BurrError) as e:
+        burr.build_batch(keys, vals, [0, 9_000_000], [8])
+    assert e.value.code == burr.ERR_INVALID
