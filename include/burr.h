@@ -238,6 +238,91 @@ int burr_stage_sort_noalloc(const uint64_t *d_keys, const void *d_values, uint64
                             uint64_t *d_sorted_keys, void *d_sorted_values, uint32_t *d_bucket_start,
                             void *stream);
 
+/*
+ * Build/query server on one device: continuous batching of independent
+ * builds with resident structures (the many-small-structures use of
+ * retrieval, Sec. 1 "Applications"; the paper describes no server: the
+ * request loop is an interface of this library around burr_build_batch).
+ *
+ * A build worker thread repeatedly takes every queued build request whose
+ * device-memory estimate fits the budget next to the resident structures and
+ * the builds in flight, and builds them with one burr_build_batch call
+ * per value width (structures larger than a batch allows get burr_build of
+ * their own).  Requests submitted while a batch runs join the next one.
+ * Payloads are copied at submission into a page-locked host region of
+ * host_staging_bytes (so that the copies to the device are DMA at link
+ * speed), or into pageable memory when the region has no room.  A query worker
+ * thread runs queries on a second stream as soon as their structure is
+ * resident, overlapping the builds.  The partition size is the server's
+ * p->partition_slots (must be > 0), so a structure's export is the one
+ * burr_build gives for its keys with the server's parameters, whatever else
+ * shared its batch.
+ */
+typedef struct burr_server burr_server;
+
+typedef struct {
+    uint64_t memory_budget;          /* device bytes for resident structures plus builds in flight (> 0) */
+    uint64_t host_staging_bytes;     /* page-locked host region for request payloads (0 = none) */
+    uint32_t max_batch_structures;   /* most structures per batch (0 = 4096) */
+    uint32_t pad;
+} burr_server_config;
+
+typedef struct {
+    uint64_t bytes_resident;         /* table bytes of the resident structures */
+    uint64_t bytes_inflight;         /* estimated bytes of the builds running now */
+    uint64_t resident_structures;
+    uint64_t queued_builds;          /* submitted, not yet admitted */
+    uint64_t queued_queries;
+    uint64_t batches;                /* burr_build_batch calls made */
+    uint64_t batched_structures;     /* structures built by those calls */
+    uint64_t staged_requests;        /* payloads copied into the page-locked region */
+    uint64_t pageable_requests;      /* payloads that did not fit it (pageable memory) */
+    uint64_t built_keys;             /* keys of the builds completed or failed */
+    double build_busy_ms;            /* host time the build worker spent building */
+    double query_busy_ms;            /* host time the query worker spent querying */
+} burr_server_stats_t;
+
+/* Start a server on the current device.  p = NULL: defaults.  The server owns
+ * two non-blocking streams and two threads until burr_server_destroy. */
+int burr_server_create(const burr_server_config *cfg, const burr_params *p, burr_server **out);
+
+/* Queue a build of n keys (distinct) with r-bit values (host memory, copied
+ * before return).  *ticket names the structure.  The admission estimate of a
+ * build is 4n(8+vb) + 2m(8+vb) + 8r(m/64) + 2^20 bytes, vb the value type's
+ * bytes and m = align64(ceil(n / load_factor) + 64); BURR_ERR_OOM if it alone
+ * exceeds the budget. */
+int burr_server_submit_build(burr_server *s, const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
+                             uint64_t *ticket);
+
+/* Queue a query of n host keys on the structure of build_ticket (which may
+ * still be queued).  `out` (host, n values of the structure's value type)
+ * must stay valid until burr_server_wait returns for *ticket. */
+int burr_server_submit_query(burr_server *s, uint64_t build_ticket, const uint64_t *keys, uint64_t n, void *out,
+                             uint64_t *ticket);
+
+/* Block until the request is done; *latency_ms (if not NULL) = time from its
+ * submission to its completion.  Returns the request's status (a failed
+ * build's error, or a query on a structure that failed to build:
+ * BURR_ERR_INVALID).  Waiting retires a query ticket; a build ticket stays
+ * valid until burr_server_release. */
+int burr_server_wait(burr_server *s, uint64_t ticket, double *latency_ms);
+
+/* The resident structure of a completed build (owned by the server; valid
+ * until burr_server_release of the ticket or burr_server_destroy). */
+int burr_server_handle(burr_server *s, uint64_t build_ticket, const burr_handle **out);
+
+/* Free a completed build's structure and return its memory to the budget.
+ * BURR_ERR_INVALID while the build is pending or queries on it are queued;
+ * a query running on it is waited for. */
+int burr_server_release(burr_server *s, uint64_t build_ticket);
+
+int burr_server_stats(burr_server *s, burr_server_stats_t *st);
+
+/* Finish the running batch and queries, fail the builds still queued
+ * (BURR_ERR_INVALID), free every structure and stop the threads.  No other
+ * call on `s` may run concurrently or follow. */
+void burr_server_destroy(burr_server *s);
+
 #ifdef __cplusplus
 }
 #endif

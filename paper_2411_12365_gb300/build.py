@@ -16,7 +16,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", INCLUDE, "-I", CSRC]
-UNITS = ["burr_api.cu", "burr_sort.cu", "burr_band.cu", "burr_query.cu", "burr_noalloc.cu"]
+UNITS = ["burr_api.cu", "burr_sort.cu", "burr_band.cu", "burr_query.cu", "burr_noalloc.cu", "burr_server.cu"]
 
 
 def _sources():
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str |
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -50,9 +50,23 @@ class Stats(C.Structure):
     ]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("memory_budget", C.c_uint64), ("host_staging_bytes", C.c_uint64),
+                ("max_batch_structures", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("bytes_resident", "bytes_inflight", "resident_structures",
+                                          "queued_builds", "queued_queries", "batches", "batched_structures",
+                                          "staged_requests", "pageable_requests", "built_keys")] + [
+        ("build_busy_ms", C.c_double), ("query_busy_ms", C.c_double)]
+
+
 EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query", "burr_size_bytes", "burr_export",
             "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
-            "burr_stage_sort", "burr_stage_sort_noalloc"]
+            "burr_stage_sort", "burr_stage_sort_noalloc", "burr_server_create", "burr_server_submit_build",
+            "burr_server_submit_query", "burr_server_wait", "burr_server_handle", "burr_server_release",
+            "burr_server_stats", "burr_server_destroy"]
 
 
 def lib_path() -> str:
@@ -97,6 +111,22 @@ def load(path: str | None = None):
         L.burr_stage_sort.restype = i
         L.burr_stage_sort_noalloc.argtypes = [p, p, u64, u32, u64, u32, u64, p, p, p, p]
         L.burr_stage_sort_noalloc.restype = i
+        L.burr_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(Params), C.POINTER(p)]
+        L.burr_server_create.restype = i
+        L.burr_server_submit_build.argtypes = [p, p, p, u64, u32, C.POINTER(u64)]
+        L.burr_server_submit_build.restype = i
+        L.burr_server_submit_query.argtypes = [p, u64, p, u64, p, C.POINTER(u64)]
+        L.burr_server_submit_query.restype = i
+        L.burr_server_wait.argtypes = [p, u64, C.POINTER(C.c_double)]
+        L.burr_server_wait.restype = i
+        L.burr_server_handle.argtypes = [p, u64, C.POINTER(p)]
+        L.burr_server_handle.restype = i
+        L.burr_server_release.argtypes = [p, u64]
+        L.burr_server_release.restype = i
+        L.burr_server_stats.argtypes = [p, C.POINTER(ServerStats)]
+        L.burr_server_stats.restype = i
+        L.burr_server_destroy.argtypes = [p]
+        L.burr_server_destroy.restype = None
         _lib = L
         return L
 
@@ -151,16 +181,21 @@ def _stream_value(s):
 
 
 class Handle:
-    """A built structure owned by the library (freed by .free() or GC)."""
+    """A built structure owned by the library (freed by .free() or GC).
+    A borrowed handle (owned=False, e.g. a server's resident structure) is
+    never freed from Python."""
 
-    def __init__(self, ptr, r):
+    def __init__(self, ptr, r, owned=True):
         self._h = C.c_void_p(ptr)
         self.r = r
+        self.owned = owned
 
     def __del__(self):
         self.free()
 
     def free(self):
+        if not getattr(self, "owned", False):
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             load().burr_free(self._h)
             self._h = C.c_void_p(None)
@@ -257,3 +292,87 @@ def stage_sort(keys, values, r: int, seed: int, layer_index: int, m: int, stream
     _check(load().burr_stage_sort(kp, values.data_ptr(), n, r, seed, layer_index, m, sk.data_ptr(),
                                   sv.data_ptr(), bs.data_ptr(), st))
     return sk, sv, bs
+
+
+def _host_array(x, dtype):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            x = x.cpu().numpy()
+    except ImportError:
+        pass
+    return np.ascontiguousarray(x).view(dtype) if np.asarray(x).dtype.itemsize == np.dtype(dtype).itemsize \
+        else np.ascontiguousarray(x, dtype=dtype)
+
+
+class Server:
+    """burr_server_*: continuous batching of builds with resident structures and
+    overlapping queries on one device (host keys, values and outputs)."""
+
+    def __init__(self, memory_budget: int, params: Params | None = None, max_batch_structures: int = 0,
+                 host_staging_bytes: int = 1 << 30, **kw):
+        if params is None:
+            params = default_params(**kw)
+        cfg = ServerConfig(memory_budget=int(memory_budget), host_staging_bytes=int(host_staging_bytes),
+                           max_batch_structures=int(max_batch_structures))
+        out = C.c_void_p()
+        _check(load().burr_server_create(C.byref(cfg), C.byref(params), C.byref(out)))
+        self._s = out
+        self._r = {}      # build ticket -> r
+        self._outs = {}   # query ticket -> output array (kept alive until waited)
+
+    def submit_build(self, keys, values, r: int) -> int:
+        k = _host_array(keys, np.uint64)
+        v = _host_array(values, value_np_dtype(r))
+        assert k.size == v.size
+        t = C.c_uint64(0)
+        _check(load().burr_server_submit_build(self._s, k.ctypes.data, v.ctypes.data, k.size, r, C.byref(t)))
+        self._r[t.value] = r
+        return t.value
+
+    def submit_query(self, build_ticket: int, keys) -> int:
+        k = _host_array(keys, np.uint64)
+        out = np.empty(k.size, dtype=value_np_dtype(self._r[build_ticket]))
+        t = C.c_uint64(0)
+        _check(load().burr_server_submit_query(self._s, build_ticket, k.ctypes.data, k.size, out.ctypes.data,
+                                               C.byref(t)))
+        self._outs[t.value] = out
+        return t.value
+
+    def wait(self, ticket: int):
+        """Block until the request is done: latency in ms for a build, (values,
+        latency ms) for a query.  Raises BurrError if the request failed."""
+        ms = C.c_double(0.0)
+        rc = load().burr_server_wait(self._s, ticket, C.byref(ms))
+        out = self._outs.pop(ticket, None)
+        _check(rc)
+        return ms.value if out is None else (out, ms.value)
+
+    def handle(self, build_ticket: int) -> Handle:
+        h = C.c_void_p()
+        _check(load().burr_server_handle(self._s, build_ticket, C.byref(h)))
+        return Handle(h.value, self._r[build_ticket], owned=False)
+
+    def release(self, build_ticket: int):
+        _check(load().burr_server_release(self._s, build_ticket))
+        self._r.pop(build_ticket, None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().burr_server_stats(self._s, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and self._s.value:
+            load().burr_server_destroy(self._s)
+            self._s = C.c_void_p(None)
+            self._outs.clear()
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "burr_internal.cuh"
@@ -100,17 +101,22 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Keep freed stream-ordered memory in the current device's pool (once per
+// device; callers may be on several host threads).
 void keep_pool_memory() {
-    static bool done = false;
-    if (done) return;
+    static std::mutex mu;
+    static bool done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    done = true;
+    done[dev] = true;
 }
 
 // Stream-ordered device allocations released together.

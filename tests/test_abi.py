@@ -56,3 +56,13 @@ def test_default_params_layout(lib):
 def test_strerror(lib):
     lib.burr_strerror.restype = C.c_char_p
     assert lib.burr_strerror(-3).decode().startswith("unsolvable")
+
+
+def test_server_rejects_bad_config_without_touching_the_device(lib):
+    from paper_2411_12365_gb300 import burr
+    burr.load(os.path.join(ROOT, "paper_2411_12365_gb300", "_lib", "libburr.so"))
+    for budget, kw in ((0, {}), (1 << 30, dict(partition_slots=0))):
+        with pytest.raises(burr.BurrError) as e:
+            burr.Server(budget, **kw)
+        assert e.value.code == burr.ERR_INVALID
+    assert C.sizeof(burr.ServerConfig) == 24 and C.sizeof(burr.ServerStats) == 96
