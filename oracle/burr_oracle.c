@@ -15,6 +15,8 @@
  *   - on-the-fly Gaussian elimination bucket by bucket, bumping a prefix of a
  *     bucket on failure, the prefix given by a 2-bit threshold (four levels,
  *     one bumping nothing and one bumping the whole bucket)     (Sec. 2, "Bumping")
+ *     or by a 1+-bit threshold (one bit "anything bumped?" per bucket, the
+ *     exact threshold stored only for the buckets that bump)    (Sec. 2, threshold storage)
  *   - overloading: more equations than slots per layer          (Sec. 2, last para.)
  *   - parallel construction: the equation system is cut into partitions and the
  *     first bucket after every cut bumps at least w-1 slots, so no kept equation
@@ -216,13 +218,36 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                    uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
                    or_stats *st)
 {
+    return or_build_layer_mode(keys, vals, n, r, m, sigma, levels, B, w, cuts, ncuts, fallback,
+                               OR_THRESH_2BIT, thresh, NULL, z, bumped_keys, bumped_vals, nbumped, st);
+}
+
+/*
+ * One layer in either threshold mode.  2-bit: on the first failure at offset
+ * o the bucket's threshold becomes the smallest level above o.  1+-bit: it
+ * becomes o + 1 exactly (every row at offsets <= o is bumped, the rows above
+ * stay), so the threshold is the least t for which the bucket's rows at
+ * offsets >= t can be kept.  The first bucket after a cut starts from the
+ * forced threshold: the smallest level >= w (2-bit), exactly w (1+-bit).
+ */
+int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                        uint32_t r, uint64_t m, uint64_t sigma,
+                        const uint32_t levels[4], uint32_t B, uint32_t w,
+                        const uint64_t *cuts, uint64_t ncuts, int fallback,
+                        uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
+                        uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                        or_stats *st)
+{
     *nbumped = 0;
     if (n == 0 || m == 0) return 0;
     if (w != 64 || m % 64 != 0 || m < w) return OR_EINVAL;
     uint32_t mask = (r >= 32) ? 0xFFFFFFFFu : ((1u << r) - 1u);
     uint64_t nb = or_num_buckets(m, w, B);
     int forced = or_forced_code(levels, w);
-    if (forced < 0 && ncuts > 0) return OR_EINVAL;
+    if (mode == OR_THRESH_2BIT && forced < 0 && ncuts > 0) return OR_EINVAL;
+    if (mode != OR_THRESH_2BIT && mode != OR_THRESH_1PLUS) return OR_EINVAL;
+    if (mode == OR_THRESH_1PLUS && (B > 255 || (!fallback && !texact))) return OR_EINVAL;
+    const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w : (forced >= 0 ? levels[forced] : 0);
 
     /* 1. hash every key to its equation */
     or_row *rows = (or_row *)malloc(sizeof(or_row) * n);
@@ -240,13 +265,20 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
     uint32_t *Y = (uint32_t *)calloc(m, sizeof(uint32_t));
     int64_t *slot_of = (int64_t *)malloc(sizeof(int64_t) * n);
     if (!C || !Y || !slot_of) { free(rows); free(C); free(Y); free(slot_of); return OR_ENOMEM; }
-    if (!fallback) {
+    if (!fallback && mode == OR_THRESH_2BIT) {
         /* every bucket that starts a partition j >= 1 carries the forced level,
          * also when no key falls into it */
         memset(thresh, 0, sizeof(uint64_t) * ((nb + 31) / 32));
         for (uint64_t q = 0; q < ncuts; q++) {
             uint64_t b = cuts[q] / B;
             if (b < nb) thresh[b / 32] |= (uint64_t)forced << (2 * (b % 32));
+        }
+    }
+    if (!fallback && mode == OR_THRESH_1PLUS) {
+        memset(texact, 0, nb);
+        for (uint64_t q = 0; q < ncuts; q++) {
+            uint64_t b = cuts[q] / B;
+            if (b < nb) texact[b] = (uint8_t)w;
         }
     }
 
@@ -260,8 +292,8 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         /* rows[i..j) is bucket b in descending offset order */
         while (cut_idx < ncuts && cuts[cut_idx] < b * B) cut_idx++;
         int after_cut = (cut_idx < ncuts && cuts[cut_idx] == b * B);
-        uint32_t t = (after_cut && !fallback) ? levels[forced] : 0;
-        uint32_t code = (after_cut && !fallback) ? (uint32_t)forced : 0;
+        uint32_t t = (after_cut && !fallback) ? t_forced : 0;
+        uint32_t code = (after_cut && !fallback && mode == OR_THRESH_2BIT) ? (uint32_t)forced : 0;
         for (uint64_t k = i; k < j; k++) slot_of[k] = -1;
         for (uint64_t k = i; k < j; k++) {
             uint32_t off = (uint32_t)(rows[k].start % B);
@@ -276,9 +308,13 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                 continue;
             }
             if (fallback) { status = OR_FAIL; break; }
-            code = or_level_above(levels, off);
-            if (after_cut && code < (uint32_t)forced) code = (uint32_t)forced;
-            t = levels[code];
+            if (mode == OR_THRESH_1PLUS) {
+                t = off + 1;                 /* rows at offsets >= t were all kept */
+            } else {
+                code = or_level_above(levels, off);
+                if (after_cut && code < (uint32_t)forced) code = (uint32_t)forced;
+                t = levels[code];
+            }
             /* roll back every row of this bucket below the new threshold */
             for (uint64_t q = i; q < k; q++) {
                 uint32_t oq = (uint32_t)(rows[q].start % B);
@@ -292,8 +328,12 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         }
         if (status) break;
         if (!fallback) {
-            thresh[b / 32] &= ~(3ULL << (2 * (b % 32)));
-            thresh[b / 32] |= (uint64_t)code << (2 * (b % 32));
+            if (mode == OR_THRESH_1PLUS) {
+                texact[b] = (uint8_t)t;
+            } else {
+                thresh[b / 32] &= ~(3ULL << (2 * (b % 32)));
+                thresh[b / 32] |= (uint64_t)code << (2 * (b % 32));
+            }
             for (uint64_t k = i; k < j; k++) {
                 if ((uint32_t)(rows[k].start % B) < t) {
                     bumped_keys[*nbumped] = rows[k].key;
@@ -376,6 +416,7 @@ void or_free(or_struct *s)
     for (uint32_t l = 0; l <= OR_MAX_LAYERS; l++) {
         free(s->layer[l].thresh);
         free(s->layer[l].z);
+        free(s->layer[l].texact);
     }
     memset(s, 0, sizeof(*s));
 }
@@ -394,7 +435,9 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         !(p->levels[0] < p->levels[1] && p->levels[1] < p->levels[2] &&
           p->levels[2] < p->levels[3]) ||
         p->partition_slots % p->B != 0 || p->partition_slots == 0 ||
-        !(p->alpha > 0.0) || or_forced_code(p->levels, p->w) < 0)
+        !(p->alpha > 0.0) || or_forced_code(p->levels, p->w) < 0 ||
+        (p->threshold_mode != OR_THRESH_2BIT && p->threshold_mode != OR_THRESH_1PLUS) ||
+        (p->threshold_mode == OR_THRESH_1PLUS && p->B > 255))
         return OR_EINVAL;
     out->params = *p;
     out->n = n;
@@ -422,14 +465,17 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         uint64_t ncuts = L->nparts ? L->nparts - 1 : 0;
         uint64_t *cuts = (uint64_t *)malloc(sizeof(uint64_t) * (ncuts ? ncuts : 1));
         for (uint64_t j = 0; j < ncuts; j++) cuts[j] = (j + 1) * P;
-        L->thresh = (uint64_t *)calloc((L->nbuckets + 31) / 32 + 1, sizeof(uint64_t));
+        const int onep = p->threshold_mode == OR_THRESH_1PLUS;
+        if (onep) L->texact = (uint8_t *)calloc(L->nbuckets + 1, 1);
+        else L->thresh = (uint64_t *)calloc((L->nbuckets + 31) / 32 + 1, sizeof(uint64_t));
         L->z = (uint64_t *)calloc((L->m / 64) * p->r + 1, sizeof(uint64_t));
         uint64_t nb = 0;
-        if (!cuts || !L->thresh || !L->z) status = OR_ENOMEM;
+        if (!cuts || !(onep ? (void *)L->texact : (void *)L->thresh) || !L->z) status = OR_ENOMEM;
         else
-            status = or_build_layer(ck, cv, cn, p->r, L->m,
-                                    or_layer_seed(p->seed, l), p->levels, p->B, p->w,
-                                    cuts, ncuts, 0, L->thresh, L->z, nk, nv, &nb, st);
+            status = or_build_layer_mode(ck, cv, cn, p->r, L->m,
+                                         or_layer_seed(p->seed, l), p->levels, p->B, p->w,
+                                         cuts, ncuts, 0, p->threshold_mode, L->thresh, L->texact,
+                                         L->z, nk, nv, &nb, st);
         free(cuts);
         L->nbumped = nb;
         if (st) st->bumped[l] = nb;
@@ -476,8 +522,14 @@ uint32_t or_query_one(const or_struct *s, uint64_t key)
         or_hash(key, or_layer_seed(p->seed, L->seed_index), L->m, p->w, &st, &c);
         uint64_t b = st / p->B;
         uint32_t off = (uint32_t)(st % p->B);
-        uint32_t code = (uint32_t)((L->thresh[b / 32] >> (2 * (b % 32))) & 3ULL);
-        if (off < p->levels[code]) continue;
+        uint32_t t;
+        if (p->threshold_mode == OR_THRESH_1PLUS) {
+            t = L->texact[b];
+        } else {
+            uint32_t code = (uint32_t)((L->thresh[b / 32] >> (2 * (b % 32))) & 3ULL);
+            t = p->levels[code];
+        }
+        if (off < t) continue;
         return or_layer_eval(L->z, p->r, st, c);
     }
     const or_layer *F = &s->layer[OR_MAX_LAYERS];
@@ -499,17 +551,41 @@ void or_query(const or_struct *s, const uint64_t *keys, uint32_t *out, uint64_t 
 static uint8_t *put32(uint8_t *q, uint32_t v) { memcpy(q, &v, 4); return q + 4; }
 static uint8_t *put64(uint8_t *q, uint64_t v) { memcpy(q, &v, 8); return q + 8; }
 
+/* Number of buckets of a 1+-bit layer that bump anything (flag bit set). */
+static uint64_t or_flagged(const or_layer *L)
+{
+    uint64_t c = 0;
+    for (uint64_t b = 0; b < L->nbuckets; b++) c += L->texact[b] != 0;
+    return c;
+}
+
+/* Bytes of one bumping layer's threshold section in the export. */
+static uint64_t or_thresh_bytes(const or_params *p, const or_layer *L)
+{
+    if (p->threshold_mode == OR_THRESH_1PLUS)
+        return 8 * ((L->nbuckets + 63) / 64) + 8 + 8 * ((or_flagged(L) + 7) / 8);
+    return 8 * ((L->nbuckets + 31) / 32);
+}
+
+/*
+ * Version 1 (2-bit thresholds): per bumping layer the 2-bit code words.
+ * Version 2 (1+-bit thresholds): per bumping layer the flag words (bit b%64
+ * of word b/64 set iff bucket b bumps anything), a u64 count of flagged
+ * buckets, then their exact thresholds as bytes in bucket order, zero-padded
+ * to a multiple of 8 bytes.
+ */
 uint64_t or_export(const or_struct *s, uint8_t *buf, uint64_t cap)
 {
     const or_params *p = &s->params;
+    const int onep = p->threshold_mode == OR_THRESH_1PLUS;
     uint64_t need = 4 * 10 + 8 * 4 + (uint64_t)p->layers * 8 * 5 + 8 * 4;
     for (uint32_t l = 0; l < p->layers; l++)
-        need += 8 * ((s->layer[l].nbuckets + 31) / 32) + 8 * (s->layer[l].m / 64) * p->r;
+        need += or_thresh_bytes(p, &s->layer[l]) + 8 * (s->layer[l].m / 64) * p->r;
     need += 8 * (s->layer[OR_MAX_LAYERS].m / 64) * p->r;
     if (!buf || cap < need) return need;
     uint8_t *q = buf;
     q = put32(q, 0x52525542u); /* "BURR" */
-    q = put32(q, 1);
+    q = put32(q, onep ? 2 : 1);
     q = put32(q, p->r); q = put32(q, p->w); q = put32(q, p->B); q = put32(q, p->layers);
     for (int i = 0; i < 4; i++) q = put32(q, p->levels[i]);
     uint64_t abits; memcpy(&abits, &p->alpha, 8);
@@ -525,8 +601,22 @@ uint64_t or_export(const or_struct *s, uint8_t *buf, uint64_t cap)
     q = put64(q, s->fb_attempt);
     for (uint32_t l = 0; l < p->layers; l++) {
         const or_layer *L = &s->layer[l];
-        uint64_t nw = (L->nbuckets + 31) / 32;
-        memcpy(q, L->thresh, 8 * nw); q += 8 * nw;
+        if (onep) {
+            uint64_t nw = (L->nbuckets + 63) / 64, cnt = or_flagged(L);
+            memset(q, 0, 8 * nw);
+            for (uint64_t b = 0; b < L->nbuckets; b++)
+                if (L->texact[b]) q[b / 8] |= (uint8_t)(1u << (b % 8));   /* little-endian words */
+            q += 8 * nw;
+            q = put64(q, cnt);
+            uint64_t padded = 8 * ((cnt + 7) / 8), k = 0;
+            memset(q, 0, padded);
+            for (uint64_t b = 0; b < L->nbuckets; b++)
+                if (L->texact[b]) q[k++] = L->texact[b];
+            q += padded;
+        } else {
+            uint64_t nw = (L->nbuckets + 31) / 32;
+            memcpy(q, L->thresh, 8 * nw); q += 8 * nw;
+        }
         uint64_t nz = (L->m / 64) * p->r;
         memcpy(q, L->z, 8 * nz); q += 8 * nz;
     }
@@ -541,8 +631,16 @@ double or_overhead(const or_struct *s)
     const or_params *p = &s->params;
     if (s->n == 0) return 0.0;
     double bits = 0;
-    for (uint32_t l = 0; l < p->layers; l++)
-        bits += (double)s->layer[l].m * p->r + 2.0 * (double)s->layer[l].nbuckets;
+    /* thresholds: 2 bits per bucket, or 1 bit per bucket plus 8 bits per
+     * bucket that bumps (the exact threshold, 1..B) */
+    for (uint32_t l = 0; l < p->layers; l++) {
+        const or_layer *L = &s->layer[l];
+        bits += (double)L->m * p->r;
+        if (p->threshold_mode == OR_THRESH_1PLUS)
+            bits += (double)L->nbuckets + 8.0 * (double)or_flagged(L);
+        else
+            bits += 2.0 * (double)L->nbuckets;
+    }
     bits += (double)s->layer[OR_MAX_LAYERS].m * p->r;
     return bits / ((double)p->r * (double)s->n) - 1.0;
 }

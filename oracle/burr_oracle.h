@@ -12,6 +12,9 @@
 #define OR_UNSOLVABLE (-3)
 #define OR_FAIL (-4)
 
+#define OR_THRESH_2BIT 0u   /* four threshold levels, 2 bits per bucket */
+#define OR_THRESH_1PLUS 1u  /* exact threshold; 1 bit per bucket + the bumping buckets' thresholds */
+
 typedef struct {
     uint32_t r;                     /* value bits, 1..32 */
     uint32_t w;                     /* ribbon width, 64 */
@@ -25,12 +28,15 @@ typedef struct {
     uint64_t seed;
     double fb_slack;                /* base case m = n(1+slack)+w, x1.1 per retry */
     uint64_t cut_P[OR_MAX_LAYERS];  /* per-layer override of P (0 = P) */
+    uint32_t threshold_mode;        /* OR_THRESH_2BIT or OR_THRESH_1PLUS */
+    uint32_t pad;
 } or_params;
 
 typedef struct {
     uint64_t n, m, seed_index, nbuckets, nparts, part_slots, nbumped;
-    uint64_t *thresh;               /* ceil(nbuckets/32) words of 2-bit codes */
+    uint64_t *thresh;               /* 2-bit mode: ceil(nbuckets/32) words of 2-bit codes */
     uint64_t *z;                    /* (m/64)*r words, interleaved bit planes */
+    uint8_t *texact;                /* 1+-bit mode: exact threshold of every bucket, 0..B */
 } or_layer;
 
 typedef struct {
@@ -65,6 +71,13 @@ int or_build_layer(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                    uint64_t *thresh, uint64_t *z,
                    uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
                    or_stats *st);
+int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                        uint32_t r, uint64_t m, uint64_t sigma,
+                        const uint32_t levels[4], uint32_t B, uint32_t w,
+                        const uint64_t *cuts, uint64_t ncuts, int fallback,
+                        uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
+                        uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                        or_stats *st);
 void or_default_params(or_params *p);
 int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
              const or_params *p, or_struct *out, or_stats *st);

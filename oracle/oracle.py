@@ -26,6 +26,7 @@ _LIB_PATH = os.path.join(_BUILD, "libburr_oracle.so")
 
 MAX_LAYERS = 8
 EINVAL, ENOMEM, UNSOLVABLE, FAIL = -1, -2, -3, -4
+THRESH_2BIT, THRESH_1PLUS = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -50,14 +51,14 @@ class Params(C.Structure):
         ("layers", C.c_uint32), ("fb_max_retries", C.c_uint32),
         ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64),
         ("seed", C.c_uint64), ("fb_slack", C.c_double),
-        ("cut_P", C.c_uint64 * MAX_LAYERS),
+        ("cut_P", C.c_uint64 * MAX_LAYERS), ("threshold_mode", C.c_uint32), ("pad", C.c_uint32),
     ]
 
 
 class Layer(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in
                 ("n", "m", "seed_index", "nbuckets", "nparts", "part_slots", "nbumped")] + [
-        ("thresh", C.POINTER(C.c_uint64)), ("z", C.POINTER(C.c_uint64))]
+        ("thresh", C.POINTER(C.c_uint64)), ("z", C.POINTER(C.c_uint64)), ("texact", C.POINTER(C.c_uint8))]
 
 
 class Struct(C.Structure):
@@ -91,6 +92,12 @@ def lib():
             L.or_build_layer.restype = C.c_int
             L.or_build_layer.argtypes = [p, p, u64, u32, u64, u64, p, u32, u32, p, u64, C.c_int,
                                          p, p, p, p, C.POINTER(u64), C.POINTER(Stats)]
+            L.or_build_layer_mode.restype = C.c_int
+            L.or_build_layer_mode.argtypes = [p, p, u64, u32, u64, u64, p, u32, u32, p, u64, C.c_int,
+                                              u32, p, p, p, p, p, C.POINTER(u64), C.POINTER(Stats)]
+            L.or_struct_size.restype = u64; L.or_struct_size.argtypes = []
+            L.or_params_size.restype = u64; L.or_params_size.argtypes = []
+            L.or_layer_size.restype = u64; L.or_layer_size.argtypes = []
             L.or_default_params.restype = None; L.or_default_params.argtypes = [C.POINTER(Params)]
             L.or_build.restype = C.c_int
             L.or_build.argtypes = [p, p, u64, C.POINTER(Params), C.POINTER(Struct), C.POINTER(Stats)]
@@ -160,9 +167,10 @@ def num_partitions(m, P, min_slots):
 
 
 class LayerResult:
-    def __init__(self, status, thresh, z, bumped_keys, bumped_vals, stats):
+    def __init__(self, status, thresh, z, bumped_keys, bumped_vals, stats, texact=None):
         self.status = status
         self.thresh = thresh
+        self.texact = texact
         self.z = z
         self.bumped_keys = bumped_keys
         self.bumped_vals = bumped_vals
@@ -170,8 +178,9 @@ class LayerResult:
 
 
 def build_layer(keys, vals, r, m, sigma, cuts=(), fallback=False,
-                levels=(0, 32, 64, 128), B=128, w=64) -> LayerResult:
-    """One layer with an explicit cut list (start slots of partitions 1..K-1)."""
+                levels=(0, 32, 64, 128), B=128, w=64, mode=THRESH_2BIT) -> LayerResult:
+    """One layer with an explicit cut list (start slots of partitions 1..K-1).
+    mode THRESH_1PLUS gives exact per-bucket thresholds in .texact."""
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     vals = np.ascontiguousarray(vals, dtype=np.uint32)
     n = len(keys)
@@ -184,12 +193,19 @@ def build_layer(keys, vals, r, m, sigma, cuts=(), fallback=False,
     cu = np.array(cuts if len(cuts) else [0], dtype=np.uint64)
     nbumped = C.c_uint64()
     st = Stats()
-    rc = lib().or_build_layer(_ptr(keys), _ptr(vals), n, r, m, sigma, _ptr(lv), B, w,
-                              _ptr(cu), len(cuts), int(fallback), _ptr(thresh), _ptr(z),
-                              _ptr(bk), _ptr(bv), C.byref(nbumped), C.byref(st))
+    texact = np.zeros(nb + 1, dtype=np.uint8)
+    if mode == THRESH_2BIT:
+        rc = lib().or_build_layer(_ptr(keys), _ptr(vals), n, r, m, sigma, _ptr(lv), B, w,
+                                  _ptr(cu), len(cuts), int(fallback), _ptr(thresh), _ptr(z),
+                                  _ptr(bk), _ptr(bv), C.byref(nbumped), C.byref(st))
+    else:
+        rc = lib().or_build_layer_mode(_ptr(keys), _ptr(vals), n, r, m, sigma, _ptr(lv), B, w,
+                                       _ptr(cu), len(cuts), int(fallback), mode, _ptr(thresh),
+                                       _ptr(texact), _ptr(z), _ptr(bk), _ptr(bv), C.byref(nbumped),
+                                       C.byref(st))
     k = nbumped.value
     return LayerResult(rc, thresh[:(nb + 31) // 32], z[:(m // 64) * r], bk[:k].copy(),
-                       bv[:k].copy(), st)
+                       bv[:k].copy(), st, texact[:nb].copy() if mode != THRESH_2BIT else None)
 
 
 class OracleStruct:
@@ -223,9 +239,11 @@ class OracleStruct:
         nz = (L.m // 64) * r
         thresh = (np.ctypeslib.as_array(L.thresh, shape=(nw,)).copy()
                   if (nw and bool(L.thresh) and l != "fallback") else np.zeros(0, np.uint64))
+        texact = (np.ctypeslib.as_array(L.texact, shape=(L.nbuckets,)).copy()
+                  if (L.nbuckets and bool(L.texact) and l != "fallback") else np.zeros(0, np.uint8))
         z = np.ctypeslib.as_array(L.z, shape=(nz,)).copy() if nz else np.zeros(0, np.uint64)
         return dict(n=L.n, m=L.m, seed_index=L.seed_index, nbuckets=L.nbuckets,
-                    nparts=L.nparts, nbumped=L.nbumped, thresh=thresh, z=z)
+                    nparts=L.nparts, nbumped=L.nbumped, thresh=thresh, z=z, texact=texact)
 
     @property
     def fb_attempt(self):

@@ -8,7 +8,7 @@ import numpy as np
 def parse(buf: bytes):
     hdr = struct.unpack_from("<10I4Q", buf, 0)
     magic, version, r, w, B, layers = hdr[:6]
-    assert magic == 0x52525542 and version == 1
+    assert magic == 0x52525542 and version in (1, 2)   # 1: 2-bit thresholds, 2: 1+-bit
     off = 10 * 4 + 4 * 8
     L = []
     for _ in range(layers):
@@ -18,9 +18,22 @@ def parse(buf: bytes):
     fn, fm, fseed, fatt = struct.unpack_from("<4Q", buf, off)
     off += 32
     for d in L:
-        tw = (d["nb"] + 31) // 32
-        d["thresh"] = np.frombuffer(buf, dtype=np.uint64, count=tw, offset=off)
-        off += 8 * tw
+        if version == 1:
+            tw = (d["nb"] + 31) // 32
+            d["thresh"] = np.frombuffer(buf, dtype=np.uint64, count=tw, offset=off)
+            off += 8 * tw
+        else:
+            fw = (d["nb"] + 63) // 64
+            d["flags"] = np.frombuffer(buf, dtype=np.uint64, count=fw, offset=off)
+            off += 8 * fw
+            (cnt,) = struct.unpack_from("<Q", buf, off)
+            off += 8
+            d["exact"] = np.frombuffer(buf, dtype=np.uint8, count=cnt, offset=off)
+            off += 8 * ((cnt + 7) // 8)
+            # the whole section as words, for comparisons
+            d["thresh"] = np.concatenate([d["flags"], np.array([cnt], np.uint64),
+                                          np.frombuffer(buf, dtype=np.uint64, count=(cnt + 7) // 8,
+                                                        offset=off - 8 * ((cnt + 7) // 8))])
         zw = (d["m"] // 64) * r
         d["z"] = np.frombuffer(buf, dtype=np.uint64, count=zw, offset=off)
         off += 8 * zw
@@ -28,8 +41,17 @@ def parse(buf: bytes):
     fz = np.frombuffer(buf, dtype=np.uint64, count=zw, offset=off)
     off += 8 * zw
     assert off == len(buf)
-    return dict(r=r, w=w, B=B, layers=L, fallback=dict(n=fn, m=fm, seed_index=fseed, attempt=fatt, z=fz),
-                header=hdr)
+    return dict(r=r, w=w, B=B, version=version, layers=L,
+                fallback=dict(n=fn, m=fm, seed_index=fseed, attempt=fatt, z=fz), header=hdr)
+
+
+def exact_thresholds(layer) -> np.ndarray:
+    """Per-bucket thresholds of a 1+-bit layer from its flags and stored bytes."""
+    nb = layer["nb"]
+    flags = np.unpackbits(layer["flags"].view(np.uint8), bitorder="little")[:nb].astype(bool)
+    t = np.zeros(nb, dtype=np.int64)
+    t[flags] = layer["exact"]
+    return t
 
 
 def describe_difference(a: bytes, b: bytes) -> str:

@@ -1,14 +1,15 @@
 """The oracle's layer build against dense GF(2) brute force on tiny inputs.
 
-Covers the bumping rules of Sec. 2 (2-bit thresholds, overloading), the
-partition cuts of Sec. 3 and the back-substitution (Fig. 7's third phase).
+Covers the bumping rules of Sec. 2 (2-bit and 1+-bit thresholds,
+overloading), the partition cuts of Sec. 3 and the back-substitution (Fig. 7's
+third phase).
 """
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_2411_12365_gb300 import inputs as I
-from tests.bruteforce import check_layer, codes_of, unpack_z
+from tests.bruteforce import check_layer, check_layer_1plus, codes_of, unpack_z
 from tests.gf2 import solve_free_zero
 
 
@@ -78,3 +79,38 @@ def test_fallback_layer_is_plain_ribbon():
     # too few slots: the base case reports failure instead of bumping
     tiny = O.build_layer(k, v, r, 128, sigma, fallback=True)
     assert tiny.status == O.FAIL
+
+
+@pytest.mark.parametrize("n,alpha,P,r", [
+    (300, 1.015, 1 << 20, 8),
+    (600, 1.015, 256, 8),
+    (600, 1.30, 256, 1),
+    (900, 1.10, 384, 5),
+    (500, 0.70, 128, 16),
+    (400, 1.50, 512, 32),
+    (1500, 2.2, 256, 4),           # most buckets bump, some entirely
+])
+def test_layer_1plus_matches_dense_gf2(n, alpha, P, r):
+    k, v = _layer_inputs(n, r, seed=n + r + 7)
+    m = O.layer_slots(n, alpha)
+    K = O.num_partitions(m, P, 0)
+    cuts = [j * P for j in range(1, K)]
+    res, t = check_layer_1plus(k, v, r, m, O.layer_seed(98, 0), cuts)
+    if alpha >= 1.5:
+        # exact thresholds: values between the 2-bit levels occur
+        assert set(t) - {0, 32, 64, 128}
+
+
+def test_1plus_equals_2bit_when_nothing_bumps_but_the_cuts():
+    # underloaded: only the forced bumps after cuts remain, and both modes
+    # force exactly offsets < 64 there, so the kept sets and tables agree
+    r, n, P = 8, 400, 256
+    k, v = _layer_inputs(n, r, seed=3)
+    m = O.layer_slots(n, 0.5)
+    cuts = [j * P for j in range(1, O.num_partitions(m, P, 0))]
+    sigma = O.layer_seed(4, 0)
+    a = O.build_layer(k, v, r, m, sigma, cuts=cuts)
+    b = O.build_layer(k, v, r, m, sigma, cuts=cuts, mode=O.THRESH_1PLUS)
+    codes = codes_of(a.thresh, O.num_buckets(m))
+    assert set(codes) <= {0, 2} and list(b.texact) == [64 if c == 2 else 0 for c in codes]
+    assert np.array_equal(a.z, b.z) and sorted(a.bumped_keys) == sorted(b.bumped_keys)

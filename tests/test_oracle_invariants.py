@@ -6,6 +6,8 @@
 * the result does not depend on the input order (S is a set);
 * partitions are independent: building one partition alone gives the same
   thresholds and table bits as building it inside its layer (Sec. 3);
+* the same holds with 1+-bit thresholds, whose export stores exactly one
+  threshold byte per bucket that bumps (Sec. 2, threshold storage);
 * a key set that is not a set (a duplicated key) cannot be solved: the base
   case exhausts its retries (Sec. 4: the last layer is scaled up until it
   solves, and never does here).
@@ -18,6 +20,7 @@ import pytest
 from oracle import oracle as O
 from paper_2411_12365_gb300 import inputs as I
 from tests.bruteforce import codes_of, unpack_z
+from tests.export_format import exact_thresholds, parse
 
 
 def _kv(n, r, seed=I.KEY_SEED):
@@ -111,3 +114,41 @@ def test_invalid_params_rejected():
                 dict(levels=(0, 32, 64, 100)), dict(levels=(0, 32, 32, 128)),
                 dict(levels=(5, 32, 64, 128)), dict(alpha=0.0)):
         assert O.build(k, v, **bad).status == O.EINVAL
+
+
+@pytest.mark.parametrize("n,r,P", [(0, 8, 65536), (1, 8, 65536), (77, 3, 65536), (5000, 8, 1024),
+                                   (1 << 16, 8, 4096), (20000, 32, 2048), (30000, 1, 256)])
+def test_1plus_query_returns_stored_value(n, r, P):
+    k, v = _kv(n, r, seed=n * 37 + r)
+    s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=P, threshold_mode=O.THRESH_1PLUS)
+    assert s.ok
+    assert np.array_equal(s.query(k), v)
+
+
+def test_1plus_export_stores_the_exact_thresholds():
+    n, r, P = 1 << 15, 8, 2048
+    k, v = _kv(n, r)
+    s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=P, threshold_mode=O.THRESH_1PLUS)
+    ex = parse(s.export())
+    assert ex["version"] == 2
+    for l, L in enumerate(ex["layers"]):
+        t = exact_thresholds(L)
+        assert np.array_equal(t, s.layer(l)["texact"].astype(np.int64))
+        assert len(L["exact"]) == int(np.count_nonzero(t)) and (L["exact"] > 0).all()
+        # every partition start (a cut) is flagged with at least w
+        for j in range(1, L["parts"]):
+            assert t[j * P // 128] >= 64
+
+
+def test_1plus_permutation_invariance():
+    n, r = 20000, 8
+    k, v = _kv(n, r)
+    kw = dict(r=r, partition_slots=2048, min_partition_slots=2048, threshold_mode=O.THRESH_1PLUS)
+    a = O.build(k, v, **kw).export()
+    perm = np.random.default_rng(5).permutation(n)
+    assert O.build(k[perm], v[perm], **kw).export() == a
+
+
+def test_invalid_threshold_mode_rejected():
+    k, v = _kv(10, 8)
+    assert O.build(k, v, threshold_mode=2).status == O.EINVAL

@@ -29,6 +29,11 @@ MUTATIONS = {
                              "v ^= or_zbit(z, r, s + (uint64_t)k + 1, q) << q;"),
     "range_reduction_wrong": ("*start = or_mulhi(h, m - w + 1);", "*start = or_mulhi(h, m - w);"),
     "value_not_xored": ("y ^= Y[p];", "(void)0;"),
+    "exact_threshold_off_by_one": ("t = off + 1;                 /* rows at offsets >= t were all kept */",
+                                   "t = off;"),
+    "exact_threshold_not_stored": ("texact[b] = (uint8_t)t;", "texact[b] = (uint8_t)(t ? 1 : 0);"),
+    "exact_forced_threshold_too_small": ("const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w :",
+                                         "const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w - 1 :"),
 }
 
 

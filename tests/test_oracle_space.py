@@ -55,3 +55,27 @@ def test_overhead_per_cut_in_fig3_band(kv):
     lo = min(b for *_, b in _fig3()) / 10
     hi = max(b for *_, b in _fig3()) * 4
     assert ncuts >= 50 and lo <= per_cut <= hi
+
+
+def test_1plus_costs_less_per_cut_than_2bit(kv):
+    # Fig. 3: 1+-bit thresholds lose fewer bytes per additional thread than
+    # 2-bit thresholds (their bumping is more granular), both within the band
+    k, v = kv
+    n = len(k)
+    per_cut = {}
+    for mode in (O.THRESH_2BIT, O.THRESH_1PLUS):
+        base = O.build(k, v, r=8, partition_slots=1 << 24, min_partition_slots=0, threshold_mode=mode)
+        cut = O.build(k, v, r=8, partition_slots=1 << 14, min_partition_slots=1 << 14, threshold_mode=mode)
+        ncuts = sum(max(0, cut.layer(l)["nparts"] - 1) for l in range(4))
+        per_cut[mode] = (cut.overhead() - base.overhead()) * n / ncuts
+    fig3 = {mode: [b for nn, md, _, b in _fig3() if md == mode] for mode in ("2bit", "1plus")}
+    assert all(a < b for a, b in zip(fig3["1plus"], fig3["2bit"]))      # the paper's ordering
+    assert per_cut[O.THRESH_1PLUS] < per_cut[O.THRESH_2BIT]
+    assert min(fig3["1plus"]) / 10 <= per_cut[O.THRESH_1PLUS] <= max(fig3["1plus"]) * 4
+
+
+def test_1plus_total_overhead_below_2bit(kv):
+    k, v = kv
+    a = O.build(k, v, r=8)
+    b = O.build(k, v, r=8, threshold_mode=O.THRESH_1PLUS)
+    assert b.ok and 0.0 < b.overhead() < a.overhead()
