@@ -35,7 +35,10 @@
  *   bucket       start / 128, offset = start % 128; keys with
  *                offset < levels[code] are bumped
  *   layer slots  m = align64(ceil(n / load_factor) + 64)
- *   partitions   K = 1 if m < max(P, min_partition_slots), else floor(m/P);
+ *   partitions   P = partition_slots in layer 0, lower_partition_slots in
+ *                deeper layers (the paper's minimum buckets per thread, Sec. 3:
+ *                deep layers are small, so their partitions are short);
+ *                K = 1 if m < max(P, min_partition_slots), else floor(m/P);
  *                cut j at start slot j*P, the last partition takes the rest;
  *                partition j owns slots [j*P + 64, (j+1)*P + 64)
  *   table layout per 64-slot block, r 64-bit words; bit k of slot s is bit
@@ -84,12 +87,13 @@ typedef struct {
     uint32_t levels[4];             /* threshold levels in slots: 0 < l1 < l2 < B = l3 ({0,32,64,128});
                                        the smallest level >= w is the level forced after a cut */
     double load_factor;             /* keys per slot of a bumping layer (1.015) */
-    uint64_t partition_slots;       /* P: start slots per partition, a multiple of B (65536) */
-    uint64_t min_partition_slots;   /* layers with fewer slots are one partition (65536) */
+    uint64_t partition_slots;       /* P: start slots per partition of layer 0, a multiple of B (65536) */
+    uint64_t min_partition_slots;   /* layers with fewer slots are one partition (4096) */
     uint64_t seed;                  /* hash seed */
     double fallback_slack;          /* base case m = align64(ceil(n (1+slack)) + 64) (0.1) */
     uint32_t fallback_max_retries;  /* base-case retries, each with 10% more slots (16) */
     uint32_t flags;                 /* BURR_FLAG_* */
+    uint64_t lower_partition_slots; /* P of bumping layers >= 1, a multiple of B; 0 = partition_slots (4096) */
 } burr_params;
 
 /* Per-build statistics. */

@@ -404,7 +404,8 @@ void or_default_params(or_params *p)
     p->alpha = 1.015;   /* calibrated: ~1.0% total overhead at n=2^20, r=8 */
     p->layers = 4;
     p->partition_slots = 65536;
-    p->min_partition_slots = 65536;
+    p->min_partition_slots = 4096;
+    p->lower_partition_slots = 4096;
     p->seed = 0x5EED5EED5EED5EEDULL;
     p->fb_max_retries = 16;
     p->fb_slack = 0.1;
@@ -435,6 +436,7 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         !(p->levels[0] < p->levels[1] && p->levels[1] < p->levels[2] &&
           p->levels[2] < p->levels[3]) ||
         p->partition_slots % p->B != 0 || p->partition_slots == 0 ||
+        p->lower_partition_slots % p->B != 0 ||
         !(p->alpha > 0.0) || or_forced_code(p->levels, p->w) < 0 ||
         (p->threshold_mode != OR_THRESH_2BIT && p->threshold_mode != OR_THRESH_1PLUS) ||
         (p->threshold_mode == OR_THRESH_1PLUS && p->B > 255))
@@ -458,7 +460,13 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         L->m = or_layer_slots(cn, p->alpha, p->w);
         L->seed_index = l;
         L->nbuckets = or_num_buckets(L->m, p->w, p->B);
+        /* READING: one partition per thread with at least minbpt buckets each
+         * (Sec. 3) leaves deep layers, which are small, with partitions of
+         * just minbpt buckets; here a fixed size per layer stands for that:
+         * layer 0 is cut every partition_slots, deeper layers every
+         * lower_partition_slots */
         uint64_t P = p->partition_slots;
+        if (l > 0 && p->lower_partition_slots) P = p->lower_partition_slots;
         if (p->cut_P[l]) P = p->cut_P[l];
         L->nparts = or_num_partitions(L->m, P, p->min_partition_slots);
         L->part_slots = P;

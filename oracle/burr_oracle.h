@@ -30,6 +30,7 @@ typedef struct {
     uint64_t cut_P[OR_MAX_LAYERS];  /* per-layer override of P (0 = P) */
     uint32_t threshold_mode;        /* OR_THRESH_2BIT or OR_THRESH_1PLUS */
     uint32_t pad;
+    uint64_t lower_partition_slots; /* P of layers >= 1 (0 = partition_slots) */
 } or_params;
 
 typedef struct {

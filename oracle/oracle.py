@@ -52,6 +52,7 @@ class Params(C.Structure):
         ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64),
         ("seed", C.c_uint64), ("fb_slack", C.c_double),
         ("cut_P", C.c_uint64 * MAX_LAYERS), ("threshold_mode", C.c_uint32), ("pad", C.c_uint32),
+        ("lower_partition_slots", C.c_uint64),
     ]
 
 

@@ -36,6 +36,7 @@ class Params(C.Structure):
         ("layers", C.c_uint32), ("levels", C.c_uint32 * 4), ("load_factor", C.c_double),
         ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64), ("seed", C.c_uint64),
         ("fallback_slack", C.c_double), ("fallback_max_retries", C.c_uint32), ("flags", C.c_uint32),
+        ("lower_partition_slots", C.c_uint64),
     ]
 
 

@@ -59,6 +59,12 @@ uint64_t fallback_slots(uint64_t n, double slack, uint32_t attempt) {
 
 uint64_t num_buckets(uint64_t m, uint32_t B) { return m == 0 ? 0 : (m - kW + B) / B; }
 
+// Partition size of bumping layer l: layer 0 is cut every partition_slots,
+// deeper layers every lower_partition_slots (0: partition_slots).
+uint64_t layer_partition_slots(const burr_params &p, uint32_t l) {
+    return (l > 0 && p.lower_partition_slots) ? p.lower_partition_slots : p.partition_slots;
+}
+
 uint64_t num_partitions(uint64_t m, uint64_t P, uint64_t minP) {
     if (m == 0) return 0;
     if (m < minP || m < P) return 1;
@@ -86,6 +92,8 @@ int validate(const burr_params &p, uint32_t r) {
         return fail(BURR_ERR_INVALID, "load_factor must be positive");
     if (p.partition_slots == 0 || p.partition_slots % p.bucket_slots != 0)
         return fail(BURR_ERR_INVALID, "partition_slots must be a positive multiple of bucket_slots");
+    if (p.lower_partition_slots % p.bucket_slots != 0)
+        return fail(BURR_ERR_INVALID, "lower_partition_slots must be a multiple of bucket_slots");
     if (!(p.fallback_slack >= 0.0) || !std::isfinite(p.fallback_slack))
         return fail(BURR_ERR_INVALID, "fallback_slack must be >= 0");
     return BURR_OK;
@@ -194,7 +202,7 @@ void free_layers(burr_handle *h) {
 }
 
 LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, uint64_t sigma, uint64_t K,
-                    bool fallback) {
+                    bool fallback, uint64_t P) {
     LayerDesc L;
     memset(&L, 0, sizeof(L));
     L.n = n;
@@ -202,7 +210,7 @@ LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, ui
     L.range = m >= kW ? m - kW + 1 : 0;
     L.sigma = sigma;
     L.nb = num_buckets(m, p.bucket_slots);
-    L.P = fallback ? (m ? m : 1) : p.partition_slots;
+    L.P = fallback ? (m ? m : 1) : P;
     L.K = (uint32_t)K;
     L.r = r;
     L.B = p.bucket_slots;
@@ -336,7 +344,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         if (S.m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "layer %u needs %llu slots (>= 2^32)", l,
                                              (unsigned long long)S.m);
         S.nb = num_buckets(S.m, p.bucket_slots);
-        S.K = num_partitions(S.m, p.partition_slots, p.min_partition_slots);
+        S.K = num_partitions(S.m, layer_partition_slots(p, l), p.min_partition_slots);
         S.sigma = layer_seed(p.seed, l);
         const uint64_t tw = (S.nb + 31) / 32;
         CK(cudaMallocAsync((void **)&S.thresh, tw * 8, st), "alloc thresholds");
@@ -347,7 +355,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(ar.alloc(&bv[which], cur_n * vb), "alloc bumped values");
         }
         CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
-        const LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false);
+        const LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false, layer_partition_slots(p, l));
         const int set = (int)(l & 1);
         if (cgcap[set] < S.m) {           // second band set, sized by the first layer that uses it
             CK(ar.alloc(&cgs[set], S.m * 8), "alloc band");
@@ -414,7 +422,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(side.reuse(set), "order");
             CK(cudaMallocAsync((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");
             CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
-            const LayerDesc L = make_desc(p, r, cur_n, F.m, F.sigma, 1, true);
+            const LayerDesc L = make_desc(p, r, cur_n, F.m, F.sigma, 1, true, F.m);
             const int t0 = tm.mark();
             CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
             const int t1 = tm.mark();
@@ -500,11 +508,12 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
         const uint64_t m = fb ? fallback_slots(n[s], p.fallback_slack, (*fb_attempt)[s])
                               : layer_slots(n[s], p.load_factor);
         if (m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "structure %u needs >= 2^32 slots", s);
-        const uint64_t K = fb ? 1 : num_partitions(m, p.partition_slots, p.min_partition_slots);
+        const uint64_t Pl = layer_partition_slots(p, l);
+        const uint64_t K = fb ? 1 : num_partitions(m, Pl, p.min_partition_slots);
         const uint64_t sigma = layer_seed(p.seed, fb ? p.layers + (*fb_attempt)[s] : l);
         StructDesc D;
         memset(&D, 0, sizeof(D));
-        D.L = make_desc(p, r[s], n[s], m, sigma, K, fb);
+        D.L = make_desc(p, r[s], n[s], m, sigma, K, fb, fb ? m : Pl);
         const uint64_t ng = (D.L.nb + 63) / 64;
         if (ng > kMaxGroupsPerStruct)
             return fail(BURR_ERR_INVALID,
@@ -639,7 +648,7 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
 
     std::vector<uint64_t> n(S);
     for (uint32_t s = 0; s < S; ++s) n[s] = offsets[s + 1] - offsets[s];
-    const LayerDesc none = make_desc(p, 1, 0, 64, 0, 0, false);
+    const LayerDesc none = make_desc(p, 1, 0, 64, 0, 0, false, p.partition_slots);
     const uint64_t *cur_k = dkeys;
     const void *cur_v = dvals;
     for (uint32_t l = 0; l < p.layers; ++l) {
@@ -772,7 +781,8 @@ int burr_default_params(burr_params *p) {
     p->levels[3] = 128;
     p->load_factor = 1.015;
     p->partition_slots = 65536;
-    p->min_partition_slots = 65536;
+    p->min_partition_slots = 4096;
+    p->lower_partition_slots = 4096;
     p->seed = 0x5EED5EED5EED5EEDull;
     p->fallback_slack = 0.1;
     p->fallback_max_retries = 16;
@@ -1042,7 +1052,7 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
     burr_params p;
     burr_default_params(&p);
     cudaStream_t st = (cudaStream_t)stream;
-    const LayerDesc L = make_desc(p, r, n, m, layer_seed(seed, layer_index), 1, false);
+    const LayerDesc L = make_desc(p, r, n, m, layer_seed(seed, layer_index), 1, false, p.partition_slots);
     const uint32_t vb = value_bytes(r);
     keep_pool_memory();
     Arena ar(st);

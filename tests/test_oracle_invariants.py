@@ -152,3 +152,19 @@ def test_1plus_permutation_invariance():
 def test_invalid_threshold_mode_rejected():
     k, v = _kv(10, 8)
     assert O.build(k, v, threshold_mode=2).status == O.EINVAL
+
+
+@pytest.mark.parametrize("lower", [0, 4096, 1024, 128])
+def test_lower_layers_cut_at_their_own_partition_size(lower):
+    # deep layers are cut every lower_partition_slots (0: as layer 0), with
+    # the same minimum-size rule; queries are unaffected (cuts are invisible)
+    n, r, P, minP = 1 << 17, 8, 8192, 1024
+    k, v = _kv(n, r, seed=lower + 5)
+    s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=minP, lower_partition_slots=lower)
+    assert s.ok and np.array_equal(s.query(k), v)
+    for l in range(4):
+        L = s.layer(l)
+        Pl = P if (l == 0 or lower == 0) else lower
+        assert L["nparts"] == O.num_partitions(L["m"], Pl, minP)
+    if lower and 2 * lower <= s.layer(1)["m"]:
+        assert s.layer(1)["nparts"] > O.num_partitions(s.layer(1)["m"], P, minP)
