@@ -44,7 +44,12 @@
  *   table layout per 64-slot block, r 64-bit words; bit k of slot s is bit
  *                s%64 of word (s/64)*r + k
  *   thresholds   2-bit codes, 32 per 64-bit word, bucket b in bits
- *                [2(b%32), 2(b%32)+2) of word b/32
+ *                [2(b%32), 2(b%32)+2) of word b/32; or 1+-bit (Sec. 2): the
+ *                exact threshold t in [0, B] (rows with offset < t bumped,
+ *                the least t for which the rest insert; t >= 64 after a
+ *                cut), stored as a bit per bucket (t > 0) plus the t of the
+ *                flagged buckets, found by their rank (a count per 512
+ *                buckets) where the paper uses a small hash table
  *
  * Pointers: every key/value/output pointer may be host memory (pageable or
  * pinned) or device memory of the current device; the library detects which.
@@ -72,7 +77,8 @@ extern "C" {
 #define BURR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define BURR_ERR_INTERNAL (-6)    /* a device-side capacity check tripped */
 
-#define BURR_THRESH_2BIT 0u
+#define BURR_THRESH_2BIT 0u       /* four threshold levels, 2 bits per bucket */
+#define BURR_THRESH_1PLUS 1u      /* 1+-bit: a bit per bucket, exact thresholds of bumping buckets */
 #define BURR_MAX_LAYERS 8
 #define BURR_FLAG_TIMING 1u       /* record per-stage device times (burr_stats) */
 
@@ -82,7 +88,7 @@ typedef struct burr_handle burr_handle;
 typedef struct {
     uint32_t ribbon_width;          /* w: must be 64 */
     uint32_t bucket_slots;          /* B: start slots per bucket, 64 or 128 (128) */
-    uint32_t threshold_mode;        /* BURR_THRESH_2BIT */
+    uint32_t threshold_mode;        /* BURR_THRESH_2BIT or BURR_THRESH_1PLUS (2-bit) */
     uint32_t layers;                /* bumping layers before the base case, 0..8 (4) */
     uint32_t levels[4];             /* threshold levels in slots: 0 < l1 < l2 < B = l3 ({0,32,64,128});
                                        the smallest level >= w is the level forced after a cut */
@@ -174,12 +180,17 @@ int burr_size_bytes(const burr_handle *h, uint64_t *bytes);
 /*
  * Canonical little-endian serialisation (checkpoint format and the form in
  * which results are compared bit for bit):
- *   u32 magic 0x52525542, u32 version 1, u32 r, u32 w, u32 B, u32 layers,
+ *   u32 magic 0x52525542, u32 version (1: 2-bit, 2: 1+-bit thresholds),
+ *   u32 r, u32 w, u32 B, u32 layers,
  *   u32 levels[4], u64 seed, u64 bits of load_factor, u64 n, u64 partition_slots,
  *   per bumping layer: u64 n, m, partitions, buckets, bumped;
  *   base case: u64 n, m, seed index, attempt;
- *   per bumping layer: threshold words (ceil(buckets/32) u64), table words
- *   ((m/64)*r u64); base-case table words.
+ *   per bumping layer: thresholds, then table words ((m/64)*r u64);
+ *   base-case table words.  Thresholds are ceil(buckets/32) u64 of 2-bit
+ *   codes (version 1), or (version 2) ceil(buckets/64) u64 flag words (bit
+ *   b%64 of word b/64 set iff bucket b bumps), a u64 count of flagged
+ *   buckets and their thresholds as bytes in bucket order, zero-padded to a
+ *   multiple of 8 bytes.
  * If host_buf is NULL or *len is too small, *len is set to the size needed and
  * BURR_ERR_INVALID is returned; otherwise *len = bytes written.
  */

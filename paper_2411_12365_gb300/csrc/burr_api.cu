@@ -10,6 +10,7 @@
 #include <memory>
 #include <string>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "burr_internal.cuh"
@@ -82,7 +83,8 @@ int validate(const burr_params &p, uint32_t r) {
     if (p.ribbon_width != kW) return fail(BURR_ERR_INVALID, "ribbon_width must be 64");
     if (p.bucket_slots != 64 && p.bucket_slots != 128)
         return fail(BURR_ERR_INVALID, "bucket_slots must be 64 or 128");
-    if (p.threshold_mode != BURR_THRESH_2BIT) return fail(BURR_ERR_INVALID, "only 2-bit thresholds");
+    if (p.threshold_mode != BURR_THRESH_2BIT && p.threshold_mode != BURR_THRESH_1PLUS)
+        return fail(BURR_ERR_INVALID, "threshold_mode must be BURR_THRESH_2BIT or BURR_THRESH_1PLUS");
     if (p.layers > BURR_MAX_LAYERS) return fail(BURR_ERR_INVALID, "layers > %d", BURR_MAX_LAYERS);
     if (!(p.levels[0] == 0 && p.levels[0] < p.levels[1] && p.levels[1] < p.levels[2] &&
           p.levels[2] < p.levels[3] && p.levels[3] == p.bucket_slots))
@@ -154,9 +156,17 @@ struct Arena {
 
 struct LayerStore {
     uint64_t n = 0, m = 0, nb = 0, K = 0, nbumped = 0, seed_index = 0, sigma = 0;
-    uint64_t *thresh = nullptr;   // ceil(nb/32) words (bumping layers)
+    uint64_t *thresh = nullptr;   // 2-bit: ceil(nb/32) words (bumping layers)
+    uint64_t *flags = nullptr;    // 1+-bit: ceil(nb/64) flag words
+    uint32_t *dir = nullptr;      // 1+-bit: ceil(nb/512) ranks (into tbytes)
+    uint8_t *tbytes = nullptr;    // 1+-bit: thresholds of flagged buckets, from rank 0 of the launch
+    uint64_t nflag = 0;           // 1+-bit: flagged buckets of this layer
+    uint64_t tfirst = 0;          // 1+-bit: rank of this layer's first flagged bucket in tbytes
     uint64_t *z = nullptr;        // (m/64)*r words
 };
+
+uint64_t flag_words(uint64_t nb) { return (nb + 63) / 64; }
+uint64_t dir_blocks(uint64_t nb) { return (nb + 511) / 512; }
 
 // Device tables of a batched build, shared by the handles of its structures
 // and released with the last of them.
@@ -191,13 +201,22 @@ namespace {
 
 void free_layers(burr_handle *h) {
     if (h->shared) {                        // tables belong to the batch
-        for (auto &S : h->L) S.thresh = S.z = nullptr;
+        for (auto &S : h->L) {
+            S.thresh = S.z = S.flags = nullptr;
+            S.dir = nullptr;
+            S.tbytes = nullptr;
+        }
         return;
     }
     for (auto &S : h->L) {
         if (S.thresh) cudaFree(S.thresh);
+        if (S.flags) cudaFree(S.flags);
+        if (S.dir) cudaFree(S.dir);
+        if (S.tbytes) cudaFree(S.tbytes);
         if (S.z) cudaFree(S.z);
-        S.thresh = S.z = nullptr;
+        S.thresh = S.z = S.flags = nullptr;
+        S.dir = nullptr;
+        S.tbytes = nullptr;
     }
 }
 
@@ -218,6 +237,7 @@ LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, ui
     for (int i = 0; i < 4; ++i) L.levels[i] = p.levels[i];
     L.forced_code = (uint32_t)forced_code(p.levels);
     L.vmask = r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
+    L.mode = p.threshold_mode;
     return L;
 }
 
@@ -330,6 +350,19 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     CK(ar.alloc(&ctr, 64), "alloc counters");
     unsigned long long *bcount = (unsigned long long *)ctr;
     uint32_t *err = (uint32_t *)((char *)ctr + 8);
+    // 1+-bit thresholds: exact threshold per bucket, one segment covering
+    // every directory block of the layer
+    const bool onep = p.threshold_mode == BURR_THRESH_1PLUS;
+    uint8_t *tex = nullptr;
+    uint32_t *tcounts = nullptr, *blkseg = nullptr;
+    ThreshSeg *dseg = nullptr;
+    if (onep) {
+        CK(ar.alloc((void **)&tex, cap_nb), "alloc exact thresholds");
+        CK(ar.alloc((void **)&tcounts, dir_blocks(cap_nb) * 4), "alloc threshold counts");
+        CK(ar.alloc((void **)&blkseg, dir_blocks(cap_nb) * 4), "alloc threshold blocks");
+        CK(ar.alloc((void **)&dseg, sizeof(ThreshSeg)), "alloc threshold segment");
+        CK(cudaMemsetAsync(blkseg, 0, dir_blocks(cap_nb) * 4, st), "clear threshold blocks");
+    }
 
     const uint64_t *cur_k = dkeys;
     const void *cur_v = dvals;
@@ -346,10 +379,17 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         S.nb = num_buckets(S.m, p.bucket_slots);
         S.K = num_partitions(S.m, layer_partition_slots(p, l), p.min_partition_slots);
         S.sigma = layer_seed(p.seed, l);
-        const uint64_t tw = (S.nb + 31) / 32;
-        CK(cudaMallocAsync((void **)&S.thresh, tw * 8, st), "alloc thresholds");
+        const uint64_t tw = (S.nb + 31) / 32, nd = dir_blocks(S.nb);
+        if (onep) {
+            CK(cudaMallocAsync((void **)&S.flags, flag_words(S.nb) * 8, st), "alloc threshold flags");
+            CK(cudaMallocAsync((void **)&S.dir, (nd + 1) * 4, st), "alloc threshold directory");
+            const ThreshSeg seg{0, S.nb, 0, 0};
+            CK(cudaMemcpyAsync(dseg, &seg, sizeof(seg), cudaMemcpyHostToDevice, st), "copy threshold segment");
+        } else {
+            CK(cudaMallocAsync((void **)&S.thresh, tw * 8, st), "alloc thresholds");
+            CK(cudaMemsetAsync(S.thresh, 0, tw * 8, st), "clear thresholds");
+        }
         CK(cudaMallocAsync((void **)&S.z, (S.m / 64) * r * 8, st), "alloc table");
-        CK(cudaMemsetAsync(S.thresh, 0, tw * 8, st), "clear thresholds");
         if (!bk[which]) {
             CK(ar.alloc(&bk[which], cur_n * 8), "alloc bumped keys");
             CK(ar.alloc(&bv[which], cur_n * vb), "alloc bumped values");
@@ -368,21 +408,33 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
         tev[l][1] = tm.mark();
         CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
-                       S.thresh, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
+                       S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
         tev[l][2] = tm.mark();
+        if (onep) CK(launch_thresh_flags(tex, dseg, blkseg, (uint32_t)nd, S.flags, tcounts, S.dir, st), "flags");
         CK(side.order(st, side.side, 2), "order");
         tev[l][3] = tm.mark_on(side.side);
         CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side), "backsub");
         tev[l][4] = tm.mark_on(side.side);
         CK(side.solved(set), "order");
-        h->launches += sort_kernel_count(L) + 2;
+        h->launches += sort_kernel_count(L) + 2 + (onep ? 2 : 0);
         unsigned long long hc[2] = {0, 0};
+        uint32_t nflag = 0;
         CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
+        if (onep) CK(cudaMemcpyAsync(&nflag, S.dir + nd, 4, cudaMemcpyDeviceToHost, st), "read threshold count");
         CK(cudaStreamSynchronize(st), "layer");
         const uint32_t e = (uint32_t)(hc[1] & 0xffffffffu);
         if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the 512-slot window", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
         S.nbumped = hc[0];
+        if (onep) {
+            // exact thresholds of the flagged buckets (before the next layer's
+            // band reuses the per-bucket array)
+            S.nflag = nflag;
+            S.tfirst = 0;
+            CK(cudaMallocAsync((void **)&S.tbytes, std::max<uint64_t>(nflag, 1), st), "alloc thresholds");
+            CK(launch_thresh_compact(tex, dseg, blkseg, (uint32_t)nd, S.flags, S.dir, S.tbytes, st), "compact");
+            h->launches += 1;
+        }
         cur_k = (const uint64_t *)bk[which];
         cur_v = bv[which];
         cur_n = S.nbumped;
@@ -427,7 +479,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
             const int t1 = tm.mark();
             CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
-                           nullptr, nullptr, nullptr, bcount, err, st), "band");
+                           nullptr, nullptr, nullptr, nullptr, bcount, err, st), "band");
             h->launches += sort_kernel_count(L) + 1;
             uint32_t he = 0;
             CK(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
@@ -639,10 +691,11 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         v.nkeys = T.nkeys;
         return BURR_OK;
     };
-    auto table_alloc = [&](size_t bytes, uint64_t **d) -> cudaError_t {
-        *d = nullptr;
-        cudaError_t e = cudaMallocAsync((void **)d, std::max<size_t>(bytes, 8), st);
-        if (e == cudaSuccess) store->ptrs.push_back(*d);
+    auto table_alloc = [&](size_t bytes, auto **d) -> cudaError_t {
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(bytes, 8), st);
+        if (e == cudaSuccess) store->ptrs.push_back(q);
+        *d = static_cast<std::remove_reference_t<decltype(**d)> *>(q);
         return e;
     };
 
@@ -665,28 +718,65 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         if ((rc = ensure(T))) return rc;
         BatchView v;
         if ((rc = view(T, v))) return rc;
-        uint64_t *th, *z;
-        CK(table_alloc(T.tw * 8, &th), "alloc thresholds");
+        uint64_t *th = nullptr, *z, *tflags = nullptr;
+        uint32_t *tdir = nullptr;
+        uint8_t *tex = nullptr;
+        // 1+-bit thresholds: one segment per structure (its flag words and
+        // directory blocks) in launch-wide arrays
+        const bool onep = p.threshold_mode == BURR_THRESH_1PLUS;
+        std::vector<ThreshSeg> segs;
+        std::vector<uint32_t> blkseg;
+        uint64_t nfw = 0;
+        if (onep) {
+            for (uint32_t i = 0; i < who.size(); ++i) {
+                const StructDesc &D = T.sd[i];
+                segs.push_back(ThreshSeg{D.bucket_base, D.L.nb, nfw, (uint64_t)blkseg.size()});
+                nfw += flag_words(D.L.nb);
+                blkseg.insert(blkseg.end(), dir_blocks(D.L.nb), i);
+            }
+            CK(table_alloc(nfw * 8, &tflags), "alloc threshold flags");
+            CK(table_alloc((blkseg.size() + 1) * 4, &tdir), "alloc threshold directory");
+            CK(ar.alloc((void **)&tex, std::max<uint64_t>(T.nbuckets, 1)), "alloc exact thresholds");
+        } else {
+            CK(table_alloc(T.tw * 8, &th), "alloc thresholds");
+            CK(cudaMemsetAsync(th, 0, std::max<uint64_t>(T.tw, 1) * 8, st), "clear thresholds");
+        }
         CK(table_alloc(T.zw * 8, &z), "alloc tables");
-        CK(cudaMemsetAsync(th, 0, std::max<uint64_t>(T.tw, 1) * 8, st), "clear thresholds");
         CK(cudaMemsetAsync(ctr, 0, (size_t)S * 12 + 64, st), "clear counters");
         const int w = (int)(l & 1);
         const int t0 = tm.mark();
         CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
         const int t1 = tm.mark();
-        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th,
+        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
                        (uint64_t *)bk[w], bv2[w], bcount, err, st, &v), "band");
         const int t2 = tm.mark();
+        ThreshSeg *dsegs = nullptr;
+        uint32_t *dblk = nullptr, *tcounts = nullptr;
+        if (onep) {
+            CK(upload(ar, segs, &dsegs, st), "upload threshold segments");
+            CK(upload(ar, blkseg, &dblk, st), "upload threshold blocks");
+            CK(ar.alloc((void **)&tcounts, std::max<size_t>(blkseg.size(), 1) * 4), "alloc threshold counts");
+            CK(launch_thresh_flags(tex, dsegs, dblk, (uint32_t)blkseg.size(), tflags, tcounts, tdir, st), "flags");
+        }
         CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
         const int t3 = tm.mark();
         for (auto *h : hs) h->launches += 6;
         std::vector<unsigned long long> cnt(who.size());
+        std::vector<uint32_t> hdir(onep ? blkseg.size() + 1 : 0);
         uint32_t e = 0;
         CK(cudaMemcpyAsync(cnt.data(), bcount, cnt.size() * 8, cudaMemcpyDeviceToHost, st), "read counters");
         CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
+        if (onep) CK(cudaMemcpyAsync(hdir.data(), tdir, hdir.size() * 4, cudaMemcpyDeviceToHost, st), "read ranks");
         CK(cudaStreamSynchronize(st), "layer");
         if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the 512-slot window", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
+        uint8_t *tbytes = nullptr;
+        if (onep) {
+            CK(table_alloc(std::max<uint64_t>(hdir.back(), 1), &tbytes), "alloc thresholds");
+            CK(launch_thresh_compact(tex, dsegs, dblk, (uint32_t)blkseg.size(), tflags, tdir, tbytes, st),
+               "compact");
+            for (auto *h : hs) h->launches += 3;
+        }
         for (uint32_t i = 0; i < who.size(); ++i) {
             const uint32_t s = who[i];
             const StructDesc &D = T.sd[i];
@@ -696,7 +786,16 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             Ls.K = D.L.K;
             Ls.sigma = D.L.sigma;
             Ls.nbumped = cnt[i];
-            Ls.thresh = th + D.tw_base;
+            if (onep) {
+                const ThreshSeg &g = segs[i];
+                Ls.flags = tflags + g.fw_base;
+                Ls.dir = tdir + g.dir_base;
+                Ls.tbytes = tbytes;
+                Ls.tfirst = hdir[g.dir_base];
+                Ls.nflag = hdir[g.dir_base + dir_blocks(D.L.nb)] - hdir[g.dir_base];
+            } else {
+                Ls.thresh = th + D.tw_base;
+            }
             Ls.z = z + D.z_base;
             hs[s]->stage_ms[l][0] = tm.ms(t0, t1);
             hs[s]->stage_ms[l][1] = tm.ms(t1, t2);
@@ -725,7 +824,7 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         CK(table_alloc(T.zw * 8, &z), "alloc tables");
         CK(cudaMemsetAsync(ctr, 0, (size_t)S * 12 + 64, st), "clear counters");
         CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
-        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr,
+        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr, nullptr,
                        (uint64_t *)bk[wfb], bv2[wfb], bcount, err, st, &v), "band");
         CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
         for (auto *h : hs) h->launches += 6;
@@ -887,11 +986,17 @@ int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n
     Q.r = h->r;
     Q.B = h->p.bucket_slots;
     Q.layers = h->p.layers;
+    Q.mode = h->p.threshold_mode;
     for (int i = 0; i < 4; ++i) Q.levels[i] = h->p.levels[i];
     for (uint32_t l = 0; l <= h->p.layers; ++l) {
         Q.m[l] = h->L[l].m;
         Q.sigma[l] = layer_seed(h->p.seed, h->L[l].seed_index);
-        if (l < h->p.layers) Q.thresh[l] = h->L[l].thresh;
+        if (l < h->p.layers) {
+            Q.thresh[l] = h->L[l].thresh;
+            Q.flags[l] = h->L[l].flags;
+            Q.dir[l] = h->L[l].dir;
+            Q.tbytes[l] = h->L[l].tbytes;
+        }
         Q.z[l] = h->L[l].z;
     }
     const uint32_t vb = h->vbytes;
@@ -922,7 +1027,12 @@ int burr_size_bytes(const burr_handle *h, uint64_t *bytes) {
     uint64_t b = 64;
     for (uint32_t l = 0; l <= h->p.layers; ++l) {
         const LayerStore &S = h->L[l];
-        if (l < h->p.layers) b += 8 * ((S.nb + 31) / 32);
+        if (l < h->p.layers) {
+            if (h->p.threshold_mode == BURR_THRESH_1PLUS)
+                b += 8 * flag_words(S.nb) + 4 * dir_blocks(S.nb) + S.nflag;
+            else
+                b += 8 * ((S.nb + 31) / 32);
+        }
         b += 8 * (S.m / 64) * h->r;
     }
     *bytes = b;
@@ -942,8 +1052,15 @@ int burr_export(const burr_handle *h, void *host_buf, uint64_t *len) {
     if (!h || !len) return fail(BURR_ERR_INVALID, "NULL argument");
     const burr_params &p = h->p;
     const uint32_t r = h->r;
+    const bool onep = p.threshold_mode == BURR_THRESH_1PLUS;
+    // threshold section of a bumping layer: 2-bit code words, or (1+-bit) the
+    // flag words, the count of flagged buckets and their thresholds as bytes
+    // zero-padded to a multiple of 8
+    auto tsection = [&](const LayerStore &S) -> uint64_t {
+        return onep ? 8 * flag_words(S.nb) + 8 + 8 * ((S.nflag + 7) / 8) : 8 * ((S.nb + 31) / 32);
+    };
     uint64_t need = 4 * 10 + 8 * 4 + (uint64_t)p.layers * 8 * 5 + 8 * 4;
-    for (uint32_t l = 0; l < p.layers; ++l) need += 8 * ((h->L[l].nb + 31) / 32) + 8 * (h->L[l].m / 64) * r;
+    for (uint32_t l = 0; l < p.layers; ++l) need += tsection(h->L[l]) + 8 * (h->L[l].m / 64) * r;
     need += 8 * (h->L[p.layers].m / 64) * r;
     if (!host_buf || *len < need) {
         *len = need;
@@ -951,7 +1068,7 @@ int burr_export(const burr_handle *h, void *host_buf, uint64_t *len) {
     }
     uint8_t *q = (uint8_t *)host_buf;
     q = put32(q, 0x52525542u);
-    q = put32(q, 1);
+    q = put32(q, onep ? 2 : 1);
     q = put32(q, r);
     q = put32(q, p.ribbon_width);
     q = put32(q, p.bucket_slots);
@@ -979,8 +1096,19 @@ int burr_export(const burr_handle *h, void *host_buf, uint64_t *len) {
     for (uint32_t l = 0; l < p.layers; ++l) {
         const LayerStore &S = h->L[l];
         const uint64_t tw = (S.nb + 31) / 32, zw = (S.m / 64) * r;
-        if (tw) CK(cudaMemcpy(q, S.thresh, tw * 8, cudaMemcpyDeviceToHost), "export thresholds");
-        q += tw * 8;
+        if (onep) {
+            const uint64_t fw = flag_words(S.nb), padded = 8 * ((S.nflag + 7) / 8);
+            if (fw) CK(cudaMemcpy(q, S.flags, fw * 8, cudaMemcpyDeviceToHost), "export threshold flags");
+            q += fw * 8;
+            q = put64(q, S.nflag);
+            memset(q, 0, padded);
+            if (S.nflag)
+                CK(cudaMemcpy(q, S.tbytes + S.tfirst, S.nflag, cudaMemcpyDeviceToHost), "export thresholds");
+            q += padded;
+        } else {
+            if (tw) CK(cudaMemcpy(q, S.thresh, tw * 8, cudaMemcpyDeviceToHost), "export thresholds");
+            q += tw * 8;
+        }
         if (zw) CK(cudaMemcpy(q, S.z, zw * 8, cudaMemcpyDeviceToHost), "export table");
         q += zw * 8;
     }

@@ -56,6 +56,8 @@ struct LayerDesc {
     uint32_t levels[4];
     uint32_t forced_code;
     uint32_t vmask;      // (1 << r) - 1
+    uint32_t mode;       // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
+    uint32_t pad;
 };
 
 // One structure's layer inside a batched build: its layer descriptor and
@@ -101,7 +103,7 @@ cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
 // With a batch view (bv != nullptr) L is ignored: every partition of every
 // structure of the view is processed, bumped_count is per structure.
 cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
-                        const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh,
+                        const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh, uint8_t *texact,
                         uint64_t *bumped_keys, void *bumped_vals, unsigned long long *bumped_count,
                         uint32_t *err, cudaStream_t st, const BatchView *bv = nullptr);
 
@@ -123,11 +125,33 @@ struct QueryDesc {
     uint32_t B;
     uint32_t layers;          // bumping layers
     uint32_t levels[4];
+    uint32_t mode;            // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
     uint64_t m[BURR_MAX_LAYERS + 1];
     uint64_t sigma[BURR_MAX_LAYERS + 1];
-    const uint64_t *thresh[BURR_MAX_LAYERS];
+    const uint64_t *thresh[BURR_MAX_LAYERS];   // 2-bit codes
+    const uint64_t *flags[BURR_MAX_LAYERS];    // 1+-bit: bit per bucket
+    const uint32_t *dir[BURR_MAX_LAYERS];      // 1+-bit: rank of each 512-bucket block
+    const uint8_t *tbytes[BURR_MAX_LAYERS];    // 1+-bit: thresholds of flagged buckets (ranks index it)
     const uint64_t *z[BURR_MAX_LAYERS + 1];   // [layers] = base case
 };
+
+// 1+-bit threshold storage of one structure layer inside a launch: its
+// buckets in the band's exact-threshold array, its flag words and its
+// directory blocks (512 buckets each) in the launch-wide arrays.
+struct ThreshSeg {
+    uint64_t bucket_base, nb, fw_base, dir_base;
+};
+
+// From the exact thresholds of every bucket: flag words and, per directory
+// block, the count of flagged buckets (counts) and its exclusive prefix over
+// the launch (dir, nblk + 1 entries, dir[nblk] = total).  blk_seg maps each of
+// the nblk blocks to its segment.
+cudaError_t launch_thresh_flags(const uint8_t *texact, const ThreshSeg *segs, const uint32_t *blk_seg, uint32_t nblk,
+                                uint64_t *flags, uint32_t *counts, uint32_t *dir, cudaStream_t st);
+// The thresholds of the flagged buckets, at bytes[dir[block] + rank in block].
+cudaError_t launch_thresh_compact(const uint8_t *texact, const ThreshSeg *segs, const uint32_t *blk_seg,
+                                  uint32_t nblk, const uint64_t *flags, const uint32_t *dir, uint8_t *bytes,
+                                  cudaStream_t st);
 
 cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *keys, void *out,
                          uint64_t n, cudaStream_t st);

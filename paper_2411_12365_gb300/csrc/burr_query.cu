@@ -1,6 +1,8 @@
 // burr_query.cu -- the layered query (Sec. 2: AND the key's coefficients with
 // the table window, parity per value bit; a key below its bucket's threshold
-// was bumped and is looked up in the next layer) and the standalone hash stage.
+// was bumped and is looked up in the next layer; the threshold is a 2-bit
+// level code or, with 1+-bit thresholds, 0 unless the bucket's flag is set)
+// and the standalone hash stage.
 #include "burr_internal.cuh"
 
 namespace burr {
@@ -44,8 +46,23 @@ k_query(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uin
             const uint32_t s = (uint32_t)__umul64hi(h, m - kW + 1);
             const uint32_t b = s >> log2B;
             const uint32_t off = s & (Q.B - 1);
-            const uint32_t code = (uint32_t)(__ldg(Q.thresh[l] + (b >> 5)) >> (2 * (b & 31))) & 3u;
-            if (off < Q.levels[code]) continue;               // bumped: next layer
+            uint32_t t;
+            if (Q.mode == BURR_THRESH_1PLUS) {
+                // flag bit; a flagged bucket's threshold sits at its rank
+                const uint64_t *fl = Q.flags[l];
+                const uint64_t w = __ldg(fl + (b >> 6));
+                if ((w >> (b & 63u)) & 1ull) {
+                    uint32_t rank = __ldg(Q.dir[l] + (b >> 9));
+                    for (uint32_t k = (b >> 9) << 3; k < (b >> 6); ++k) rank += (uint32_t)__popcll(__ldg(fl + k));
+                    rank += (uint32_t)__popcll(w & ((1ull << (b & 63u)) - 1ull));
+                    t = __ldg(Q.tbytes[l] + rank);
+                } else {
+                    t = 0;
+                }
+            } else {
+                t = Q.levels[(uint32_t)(__ldg(Q.thresh[l] + (b >> 5)) >> (2 * (b & 31))) & 3u];
+            }
+            if (off < t) continue;                             // bumped: next layer
             v = eval_window(Q.z[l], Q.r, s, mix64(h + Q.sigma[l]) | 1ull);
             break;
         }

@@ -96,3 +96,20 @@ def test_batch_rejects_too_large_structure():
     with pytest.raises(burr.BurrError) as e:
         burr.build_batch(keys, vals, [0, 9_000_000], [8])
     assert e.value.code == burr.ERR_INVALID
+
+
+def test_batch_1plus_thresholds():
+    # each structure of a 1+-bit batch equals its solo build and the oracle
+    rng = np.random.default_rng(5)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(100), np.log(60000), size=30))]
+    sizes[4] = 0
+    rs = [int(x) for x in rng.choice([1, 3, 8], size=len(sizes))]
+    hs, keys, vals, offs = _check_batch(sizes, rs, partition_slots=2048, min_partition_slots=2048,
+                                        threshold_mode=burr.THRESH_1PLUS)
+    k_np = keys.cpu().numpy().view(np.uint64)
+    v_np = vals.cpu().numpy().astype(np.uint32)
+    for s in (0, 7, len(sizes) - 1):
+        a, b = int(offs[s]), int(offs[s + 1])
+        ref = O.build(k_np[a:b], v_np[a:b] & ((1 << rs[s]) - 1), r=rs[s], partition_slots=2048,
+                      min_partition_slots=2048, threshold_mode=O.THRESH_1PLUS)
+        assert hs[s].export() == ref.export(), describe_difference(hs[s].export(), ref.export())

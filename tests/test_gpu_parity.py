@@ -204,3 +204,45 @@ def test_full_size_1e8_sampled_partitions_and_invariants():
         b0, b1 = lo // 128, (hi + 127) // 128
         tw = lambda t, b: (int(t[b // 32]) >> (2 * (b % 32))) & 3  # noqa: E731
         assert [tw(res.thresh, b) for b in range(b0, b1)] == [tw(L0["thresh"], b) for b in range(b0, b1)]
+
+
+# 1+-bit thresholds (Sec. 2): exact per-bucket thresholds, exports bit-equal
+
+ONEP_CASES = [
+    (0, 8, {}), (1, 8, {}), (100, 3, {}),
+    (65573, 8, dict(partition_slots=4096, min_partition_slots=4096)),       # ragged tail
+    (1 << 20, 8, {}),
+    (200_003, 16, dict(partition_slots=8192, min_partition_slots=8192)),
+    (100_000, 32, dict(partition_slots=2048, min_partition_slots=2048)),
+    (90_000, 4, dict(partition_slots=128, min_partition_slots=0)),          # a cut at every bucket
+    (30_000, 8, dict(layers=1, partition_slots=2048, min_partition_slots=2048)),
+]
+
+
+@pytest.mark.parametrize("n,r,params", ONEP_CASES)
+def test_1plus_build_matches_oracle(n, r, params):
+    _check_build(n, r, threshold_mode=burr.THRESH_1PLUS, **params)
+
+
+@pytest.mark.parametrize("alpha,P", [(1.3, 256), (1.6, 4096), (2.2, 1024), (0.8, 65536)])
+def test_1plus_overloaded_layers_match_oracle(alpha, P):
+    h, ref, *_ = _check_build(60_000, 8, threshold_mode=burr.THRESH_1PLUS, load_factor=alpha,
+                              partition_slots=P, min_partition_slots=0)
+    if alpha >= 1.6:
+        from tests.export_format import exact_thresholds
+        t = np.concatenate([exact_thresholds(L) for L in parse(h.export())["layers"] if L["nb"]])
+        assert set(np.unique(t)) - {0, 32, 64, 128}        # thresholds between the 2-bit levels
+
+
+def test_1plus_10m_whole_structure_and_space():
+    n, r = 10_000_000, 8
+    keys, vals = _kv(n, r, seed=99)
+    h1 = burr.build(keys, vals, r, threshold_mode=burr.THRESH_1PLUS)
+    ref = O.build(_u64(keys), _vals_np(vals), r=r, threshold_mode=O.THRESH_1PLUS)
+    got, want = h1.export(), ref.export()
+    assert got == want, describe_difference(got, want)
+    assert torch.equal(h1.query(keys), vals)
+    neg = I.keys_torch(1 << 20, DEV, seed=99, offset=n)
+    assert np.array_equal(_vals_np(h1.query(neg)), ref.query(_u64(neg)))
+    h2 = burr.build(keys, vals, r)
+    assert h1.size_bytes() < h2.size_bytes()               # the point of 1+-bit thresholds

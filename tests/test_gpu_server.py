@@ -177,3 +177,15 @@ def test_server_destroy_with_pending_work():
         srv2.wait(t)
         out, _ = srv2.wait(srv2.submit_query(t, k))
         assert np.array_equal(out, v)
+
+
+def test_server_1plus_thresholds():
+    params = dict(PARAMS, threshold_mode=burr.THRESH_1PLUS)
+    reqs = [_request(70 + i, n, 8) for i, n in enumerate((500, 20_000, 60_000, 3_000))]
+    with burr.Server(8 << 30, **params) as srv:
+        ts = [srv.submit_build(k, v, 8) for k, v in reqs]
+        for t, (k, v) in zip(ts, reqs):
+            srv.wait(t)
+            assert srv.handle(t).export() == _oracle(k, v, 8, threshold_mode=O.THRESH_1PLUS).export()
+            out, _ = srv.wait(srv.submit_query(t, k))
+            assert np.array_equal(out, v)
