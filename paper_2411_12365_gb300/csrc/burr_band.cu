@@ -21,16 +21,15 @@
 //     rows is independent whenever a superset is, so each probe inserts the
 //     rows of [mid, t_ok) on top of those already kept and either keeps them
 //     (t_ok = mid) or rolls them back (t_fail = mid).
-//   * A set is inserted as a stream.  Each lane takes the next unclaimed row
-//     of the set and eliminates it on its own: one step reads the ring slot
-//     of the row's leading bit and XORs in the stored row and right-hand
-//     side; an empty slot is claimed with one 128-bit compare-and-swap (row
-//     and right-hand side stored in one atomic write), which returns what
-//     another lane stored there first if it lost the race.  This is a
-//     sequential insertion in the order the rows are stored: every slot a row
-//     eliminated against was occupied when read and stays so, and a row is
-//     stored only on a slot that was still empty.  Stored slots carry a tag
-//     of their set, so a dependent set is rolled back by clearing its tag.
+//   * A set is inserted as a stream.  Each lane takes the next row of the set
+//     (a shared-memory counter) and eliminates it on its own, with no
+//     per-step vote or barrier: one step is one 128-bit compare-and-swap on
+//     the ring slot of the row's leading bit, which either claims the slot if
+//     it is empty (row and right-hand side stored in one atomic write) or
+//     returns the stored row and right-hand side to XOR with.  This is a
+//     sequential insertion in claim order: every slot a row eliminated
+//     against was occupied when read and stays so, and a row is stored only
+//     on a slot that was still empty.
 //   * Rows are staged per bucket in shared memory in ascending offset order
 //     (a counting sort on the 7-bit offset), so each threshold band is a
 //     contiguous range and rows that run through the dense overflow of the
@@ -52,21 +51,21 @@ constexpr int kBandWarps = 4;           // partitions per CTA
 constexpr unsigned kFull = 0xffffffffu;
 
 constexpr unsigned long long kYValid = 1ull << 32;   // marks a stored right-hand side
-constexpr unsigned long long kYRhs = 0xffffffffull;   // right-hand side bits of a slot's y
-constexpr int kTagShift = 40;                         // y bits 40..55: tag of the set that stored it
 
 struct alignas(16) RingSlot {
     unsigned long long c;   // stored coefficient row (bit 0 = pivot), 0 = empty
-    unsigned long long y;   // set tag << 40 | kYValid | right-hand side (low r bits); 0 = empty
+    unsigned long long y;   // kYValid | right-hand side (low r bits); 0 = empty
 };
 
 struct BandWarpSmem {
     RingSlot ring[kRing];          // live band window
+    uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
     unsigned long long rc[kStage]; // staged coefficient rows, ascending offset
     uint32_t ry[kStage];           // staged right-hand sides
     uint8_t ro[kStage];            // staged offsets
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
-    uint32_t next;                 // next unclaimed staged row of the current set
+    uint32_t next;                 // next staged row to hand out
+    uint32_t ncommit;              // entries of clist
     uint32_t flag;                 // 1 = dependent set, 2 = ring overflow
 };
 
@@ -100,17 +99,12 @@ struct Ctx {
 
 enum { kOk = 0, kDependent = 1, kOverflow = 2 };
 
-// Clear every slot the set with this tag stored.  All of them lie in the
-// window [bB, bB + kRing): pivots never move left of their start slot and a
-// pivot past the window is an overflow.
-__device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t bB, unsigned long long tag, int lane) {
+__device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int lane) {
     __syncwarp();
-    for (uint32_t k = (uint32_t)lane; k < (uint32_t)kRing; k += 32) {
-        RingSlot &slot = S.ring[(bB + k) & kRingMask];
-        if ((slot.y & (0xffffull << kTagShift)) == tag && slot.c != 0ull) {
-            slot.c = 0;
-            slot.y = 0;
-        }
+    for (uint32_t i = lane; i < ncommit; i += 32) {
+        const uint32_t ri = S.clist[i];
+        S.ring[ri].c = 0;
+        S.ring[ri].y = 0;
     }
     __syncwarp();
 }
@@ -188,29 +182,13 @@ __device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, u
                  : "memory");
 }
 
-// 128-bit shared load of a ring slot.  Only this warp touches its ring and
-// its shared-memory operations complete in issue order, so a slot read here
-// holds either nothing or a whole stored (row, right-hand side).
-__device__ __forceinline__ void slot_load(const RingSlot *slot, unsigned long long &c, unsigned long long &y) {
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
-    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c), "=l"(y) : "r"(addr) : "memory");
-}
-
-// Stream staged rows [lo, hi) (index range) into the band.  Each lane
-// eliminates one row at a time and takes the next unclaimed row of the set
-// when its row is stored; stored slots carry the set's tag (bits 40..55 of
-// y) for a rollback.  Returns kOk, kDependent or kOverflow; nothing is
-// rolled back here.
-//
-// A step reads the slot of the row's leading bit with a plain load; only a
-// slot that looks empty (or not yet complete) is claimed with a 128-bit
-// compare-and-swap, which either stores the row or returns what another lane
-// stored there first.  Occupied slots stay occupied while a set is inserted,
-// so most steps need no atomic.  The loop is warp-uniform: all lanes take
-// each step together (a lane without a row idles), so lanes on different
-// paths never run their steps apart.
-__device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane,
-                             unsigned long long tag) {
+// Each lane eliminates its own rows; a step is one 128-bit CAS that claims an
+// empty slot or returns the stored (row, right-hand side).
+// Stream staged rows [lo, hi) (index range) into the band; stored ring
+// indices are appended to S.clist (S.ncommit).  Returns kOk, kDependent or
+// kOverflow; nothing is rolled back here.  Every lane eliminates its own row
+// (one slot_cas per step) and takes the next row when its row is stored.
+__device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
     if (lane == 0) {
         S.next = lo + 32u;
@@ -223,37 +201,32 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
     uint32_t pos = 0;
     if (has) {
         cur = S.rc[idx];
-        y = tag | kYValid | S.ry[idx];
+        y = kYValid | S.ry[idx];
         pos = bB + S.ro[idx];
     }
     volatile uint32_t *vflag = &S.flag;
-    while (__any_sync(kFull, has)) {
-        if (!has) continue;
-        RingSlot *slot = &S.ring[pos & kRingMask];
+    while (has) {
         unsigned long long oc, oy;
-        slot_load(slot, oc, oy);
-        if (oc == 0ull || !(oy & kYValid)) {
-            slot_cas(slot, cur, y, oc, oy);
-            if (oc == 0ull) {                    // stored: take the next row of the set
-                has = false;
-                if (*vflag == 0u) {
-                    idx = atomicAdd(&S.next, 1u);
-                    if (idx < hi) {
-                        cur = S.rc[idx];
-                        y = tag | kYValid | S.ry[idx];
-                        pos = bB + S.ro[idx];
-                        has = true;
-                    }
+        slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
+        if (oc == 0ull) {
+            S.clist[atomicAdd(&S.ncommit, 1u)] = (uint16_t)(pos & kRingMask);
+            has = false;
+            if (*vflag == 0u) {
+                idx = atomicAdd(&S.next, 1u);
+                if (idx < hi) {
+                    cur = S.rc[idx];
+                    y = kYValid | S.ry[idx];
+                    pos = bB + S.ro[idx];
+                    has = true;
                 }
-                continue;
             }
+            continue;
         }
         cur ^= oc;
-        y ^= oy & kYRhs;
+        y ^= oy & ~kYValid;
         if (cur == 0ull) {
             atomicOr(&S.flag, 1u);
-            has = false;
-            continue;
+            break;
         }
         const uint32_t lo32 = (uint32_t)cur;
         const int tz = lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(cur >> 32));
@@ -261,7 +234,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         pos += (uint32_t)tz;
         if (pos - bB >= (uint32_t)kRing) {
             atomicOr(&S.flag, 2u);
-            has = false;
+            break;
         }
     }
     __syncwarp();
@@ -273,26 +246,46 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 // set; on a dependency or overflow every row this call stored is removed.
 template <typename V>
 __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
-                          uint32_t bB, uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane,
-                          uint32_t &settag) {
-    // a fresh tag per set; slots of earlier sets still in the window (at most
-    // a few buckets' worth of sets) carry other tags
-    settag = (settag + 1u) & 0xffffu;
-    const unsigned long long tag = (unsigned long long)settag << kTagShift;
+                          uint32_t bB, uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
+    if (lane == 0) S.ncommit = 0;
+    __syncwarp();
     for (uint32_t base = rs; base < re; base += kStage) {
         const uint32_t cnt = min((uint32_t)kStage, re - base);
         if (staged_base != base) {
             stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
-        const int rc = stream_insert(S, S.first[olo], S.first[ohi], bB, lane, tag);
+        const int rc = stream_insert(S, S.first[olo], S.first[ohi], bB, lane);
         if (rc != kOk) {
-            rollback(S, bB, tag, lane);
+            rollback(S, S.ncommit, lane);
             if (rc == kOverflow && lane == 0) atomicOr(a.err, kErrRingOverflow);
             return rc;
         }
     }
     return kOk;
+}
+
+// 1+-bit threshold of a bucket whose rows at offsets >= forced are dependent:
+// the least t for which the rows at offsets >= t insert, those rows left
+// inserted.  Rows at offsets >= t_fail are dependent, those >= t_ok are kept;
+// exact thresholds are mostly small (a few rows at the lowest offsets), so the
+// first probe keeps all but the lowest 16 offsets and bisection follows.
+// Returns B + 1 on a ring overflow.
+template <typename V>
+__device__ __forceinline__ uint32_t exact_threshold(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs,
+                                                 uint32_t re, uint32_t bB, uint32_t forced, uint32_t &staged,
+                                                 int lane) {
+    uint32_t t_fail = forced, t_ok = x.L.B;
+    bool first = true;
+    while (t_ok - t_fail > 1) {
+        const uint32_t mid = (first && t_fail + 16u < t_ok) ? t_fail + 16u : (t_fail + t_ok) >> 1;
+        first = false;
+        const int rc = insert_set(S, a, x, rs, re, bB, mid, t_ok, staged, lane);
+        if (rc == kOverflow) return x.L.B + 1u;
+        if (rc == kOk) t_ok = mid;
+        else t_fail = mid;
+    }
+    return t_ok;
 }
 
 // Rows of the bucket below threshold t leave for the next layer.
@@ -337,7 +330,9 @@ __device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, con
     __syncwarp();
 }
 
-template <typename V>
+// kExact: 1+-bit thresholds (exact per bucket) instead of 2-bit codes; a
+// template parameter so that each mode gets its own register allocation.
+template <typename V, bool kExact>
 __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -386,7 +381,6 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
 
     uint64_t flushed = own_lo;
     uint64_t tword = 0, twi = b0 >> 5;
-    uint32_t settag = 0;
     for (uint64_t b = b0; b < b1; ++b) {
         const uint64_t bB = b * L.B;
         if (bB > flushed) {
@@ -394,41 +388,28 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
             flushed = bB;
         }
         const bool cut = (part > 0 && b == b0 && !L.fallback);
-        const uint32_t forced = cut ? (L.mode == BURR_THRESH_1PLUS ? (uint32_t)kW : flevel) : 0;
+        const uint32_t forced = cut ? (kExact ? (uint32_t)kW : flevel) : 0;
         uint32_t code = cut ? fcode : 0;
         uint32_t texact = forced;
         const uint32_t rs = a.bstart[x.bucket_base + b], re = a.bstart[x.bucket_base + b + 1];
         if (re > rs) {
             uint32_t staged = 0xffffffffu;
-            int rc = insert_set(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane, settag);
+            int rc = insert_set(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
             if (rc == kOverflow) return;
             if (rc == kDependent) {
                 if (L.fallback) {
                     if (lane == 0) atomicOr(x.fail ? x.fail : a.err, kErrUnsolvable);
                     return;
                 }
-                if (L.mode == BURR_THRESH_1PLUS) {
-                    // rows at offsets >= t_fail are dependent, those >= t_ok are
-                    // kept; exact thresholds are mostly small (a few rows at the
-                    // lowest offsets), so the first probe keeps all but the
-                    // lowest 16 offsets and bisection follows
-                    uint32_t t_fail = forced, t_ok = L.B;
-                    bool first = true;
-                    while (t_ok - t_fail > 1) {
-                        const uint32_t mid = (first && t_fail + 16u < t_ok) ? t_fail + 16u : (t_fail + t_ok) >> 1;
-                        first = false;
-                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, mid, t_ok, staged, lane, settag);
-                        if (rc2 == kOverflow) return;
-                        if (rc2 == kOk) t_ok = mid;
-                        else t_fail = mid;
-                    }
-                    texact = t_ok;
+                if (kExact) {
+                    texact = exact_threshold(S, a, x, rs, re, (uint32_t)bB, forced, staged, lane);
+                    if (texact > L.B) return;   // ring overflow (recorded)
                 } else {
                     code = 3;
                     for (int k = 2; k >= 0; --k) {
                         if (lv[k + 1] <= forced) break;
                         const uint32_t lo = max(lv[k], forced), hi = lv[k + 1];
-                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lo, hi, staged, lane, settag);
+                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lo, hi, staged, lane);
                         if (rc2 == kOverflow) return;
                         if (rc2 == kDependent) {
                             code = (uint32_t)k + 1;
@@ -438,10 +419,10 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                     }
                 }
             }
-            const uint32_t t = L.mode == BURR_THRESH_1PLUS ? texact : lv[code];
+            const uint32_t t = kExact ? texact : lv[code];
             if (!L.fallback && t > 0) emit_bumped(a, x, rs, re, (uint32_t)bB, t, lane);
         }
-        if (!L.fallback && L.mode == BURR_THRESH_1PLUS) {
+        if (kExact && !L.fallback) {
             if (lane == 0) a.texact[x.bucket_base + b] = (uint8_t)texact;
             continue;
         }
@@ -570,7 +551,11 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
     a.err = err;
     const uint64_t parts = bv ? bv->nparts : L.K;
     const unsigned grid = (unsigned)((parts + kBandWarps - 1) / kBandWarps);
-    k_band<V><<<grid, 32 * kBandWarps, 0, st>>>(a);
+    // the threshold mode is one for the whole launch (a batch shares its parameters)
+    if (L.mode == BURR_THRESH_1PLUS && !L.fallback)
+        k_band<V, true><<<grid, 32 * kBandWarps, 0, st>>>(a);
+    else
+        k_band<V, false><<<grid, 32 * kBandWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 
