@@ -186,6 +186,7 @@ def oracle_sample(n_s: int, r: int, P: int, minP: int = 4096, lowP: int = 4096, 
     out = s.query(q)
     dt = time.perf_counter() - t0
     assert s.ok and np.array_equal(out[: n_s // 2], v[: n_s // 2])
+    oracle_sample.xor_steps_per_row = s.stats.xor_steps / max(s.stats.inserted, 1)
     return dt
 
 
@@ -622,6 +623,9 @@ def main():
         line["cpu_baseline"] = {"value": a.cpu_sample / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"serial C oracle: build + query of {a.cpu_sample} keys "
                                           f"(same r, P, load; {dt:.1f} s)"}
+        # the dependent chain behind the band kernel's latency bound: row XORs
+        # per insertion attempt of the serial elimination
+        line["breakdown"]["oracle_xor_steps_per_row"] = oracle_sample.xor_steps_per_row
     if rank == 0:
         print(json.dumps(line), flush=True)
 

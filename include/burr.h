@@ -122,6 +122,27 @@ typedef struct {
     uint64_t kernel_launches;                   /* CUDA kernels this build launched */
 } burr_stats_t;
 
+/*
+ * Device memory.  By default the library takes its device memory (build
+ * scratch, the tables of every handle, query staging, the server's batch
+ * inputs) from the current device's stream-ordered pool.  burr_set_allocator
+ * routes it through the caller's allocator instead, e.g. PyTorch's caching
+ * allocator (an interface of this library; the paper has no counterpart):
+ *   alloc(bytes, stream, ctx)  device memory usable in stream order on
+ *                              `stream` (a cudaStream_t), or NULL (the call
+ *                              that needed it fails with BURR_ERR_OOM);
+ *   free(ptr, stream, ctx)     release after the work enqueued on `stream`;
+ *                              stream NULL: no work uses it any more.
+ * Both NULL restores the built-in pool.  Returns BURR_ERR_INVALID if exactly
+ * one of alloc/free is NULL, or while blocks from the current allocator are
+ * still held (handles not freed, a build running): set it before building.
+ * The callbacks may be called from any thread that calls the library and
+ * from the server's worker threads.
+ */
+typedef void *(*burr_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
+typedef void (*burr_free_fn)(void *ptr, void *stream, void *ctx);
+int burr_set_allocator(burr_alloc_fn alloc, burr_free_fn free, void *ctx);
+
 /* Fill *p with the defaults above.  Returns BURR_OK or BURR_ERR_INVALID (p NULL). */
 int burr_default_params(burr_params *p);
 

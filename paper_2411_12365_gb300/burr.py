@@ -68,7 +68,11 @@ EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query
             "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
             "burr_stage_sort", "burr_stage_sort_noalloc", "burr_server_create", "burr_server_submit_build",
             "burr_server_submit_query", "burr_server_wait", "burr_server_handle", "burr_server_release",
-            "burr_server_stats", "burr_server_destroy"]
+            "burr_server_stats", "burr_server_destroy", "burr_set_allocator"]
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_allocator_refs = []   # keeps the installed callbacks alive
 
 
 def lib_path() -> str:
@@ -129,6 +133,8 @@ def load(path: str | None = None):
         L.burr_server_stats.restype = i
         L.burr_server_destroy.argtypes = [p]
         L.burr_server_destroy.restype = None
+        L.burr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, p]
+        L.burr_set_allocator.restype = i
         _lib = L
         return L
 
@@ -378,3 +384,36 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def set_allocator(alloc=None, free=None):
+    """burr_set_allocator: route the library's device memory through
+    alloc(bytes, stream) -> int pointer (0 on failure) and free(ptr, stream);
+    both None restores the built-in pool.  Raises while blocks are held."""
+    if (alloc is None) != (free is None):
+        raise ValueError("alloc and free must both be given or both None")
+    if alloc is None:
+        _check(load().burr_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        _allocator_refs.clear()
+        return
+
+    def a(n, stream, ctx):
+        try:
+            return int(alloc(int(n), int(stream or 0))) or None
+        except Exception:
+            return None
+
+    def f(ptr, stream, ctx):
+        free(int(ptr), int(stream or 0))
+
+    fa, ff = _ALLOC_FN(a), _FREE_FN(f)
+    _check(load().burr_set_allocator(fa, ff, None))
+    _allocator_refs[:] = [fa, ff]
+
+
+def use_torch_allocator(device=None):
+    """Back the library's device memory with PyTorch's caching allocator."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    set_allocator(lambda n, stream: torch.cuda.caching_allocator_alloc(n, dev, stream),
+                  lambda ptr, stream: torch.cuda.caching_allocator_delete(ptr))

@@ -3,6 +3,7 @@
 // export and statistics.  Every step of the method runs in the kernels of
 // burr_sort.cu, burr_band.cu and burr_query.cu; this file only sizes layers,
 // allocates, launches and reads back one counter per layer.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -129,28 +130,86 @@ void keep_pool_memory() {
     done[dev] = true;
 }
 
-// Stream-ordered device allocations released together.
+// Device memory of the library: the caller's allocator when one is set
+// (burr_set_allocator), else the device's stream-ordered pool.  Every block
+// the library holds is counted, so the allocator cannot change under it.
+struct AllocHook {
+    burr_alloc_fn alloc = nullptr;
+    burr_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocHook g_hook;
+std::atomic<int64_t> g_live{0};
+
+AllocHook current_hook() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_hook;
+}
+
+}  // namespace
+
+// Stream-ordered allocation usable on `st`.
+cudaError_t burr::dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    const AllocHook h = current_hook();
+    cudaError_t e;
+    if (h.alloc) {
+        *p = h.alloc((uint64_t)bytes, (void *)st, h.ctx);
+        e = *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    } else {
+        e = cudaMallocAsync(p, bytes, st);
+    }
+    if (e == cudaSuccess) g_live.fetch_add(1);
+    return e;
+}
+
+// Release after the work enqueued on `st` (build scratch).
+void burr::dev_free_async(void *p, cudaStream_t st) {
+    if (!p) return;
+    const AllocHook h = current_hook();
+    if (h.free) h.free(p, (void *)st, h.ctx);
+    else cudaFreeAsync(p, st);
+    g_live.fetch_sub(1);
+}
+
+// Release a handle's table: work on any stream may still read it, so wait for
+// the device first (as cudaFree does).
+void burr::dev_free_sync(void *p) {
+    if (!p) return;
+    const AllocHook h = current_hook();
+    if (h.free) {
+        cudaDeviceSynchronize();
+        h.free(p, nullptr, h.ctx);
+    } else {
+        cudaFree(p);
+    }
+    g_live.fetch_sub(1);
+}
+
+namespace {
+
+// Device allocations released together, in stream order.
 struct Arena {
     cudaStream_t st;
     std::vector<void *> ptrs;
     explicit Arena(cudaStream_t s) : st(s) {}
     cudaError_t alloc(void **p, size_t bytes) {
-        *p = nullptr;
         if (bytes == 0) bytes = 256;
-        cudaError_t e = cudaMallocAsync(p, bytes, st);
+        cudaError_t e = dev_alloc(p, bytes, st);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
     void release(void *p) {
         for (auto &q : ptrs)
             if (q == p) {
-                cudaFreeAsync(q, st);
+                dev_free_async(q, st);
                 q = nullptr;
             }
     }
     ~Arena() {
         for (void *p : ptrs)
-            if (p) cudaFreeAsync(p, st);
+            if (p) dev_free_async(p, st);
     }
 };
 
@@ -173,8 +232,7 @@ uint64_t dir_blocks(uint64_t nb) { return (nb + 511) / 512; }
 struct BatchStorage {
     std::vector<void *> ptrs;
     ~BatchStorage() {
-        for (void *p : ptrs)
-            if (p) cudaFree(p);
+        for (void *p : ptrs) dev_free_sync(p);
     }
 };
 
@@ -209,11 +267,11 @@ void free_layers(burr_handle *h) {
         return;
     }
     for (auto &S : h->L) {
-        if (S.thresh) cudaFree(S.thresh);
-        if (S.flags) cudaFree(S.flags);
-        if (S.dir) cudaFree(S.dir);
-        if (S.tbytes) cudaFree(S.tbytes);
-        if (S.z) cudaFree(S.z);
+        dev_free_sync(S.thresh);
+        dev_free_sync(S.flags);
+        dev_free_sync(S.dir);
+        dev_free_sync(S.tbytes);
+        dev_free_sync(S.z);
         S.thresh = S.z = S.flags = nullptr;
         S.dir = nullptr;
         S.tbytes = nullptr;
@@ -381,15 +439,15 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         S.sigma = layer_seed(p.seed, l);
         const uint64_t tw = (S.nb + 31) / 32, nd = dir_blocks(S.nb);
         if (onep) {
-            CK(cudaMallocAsync((void **)&S.flags, flag_words(S.nb) * 8, st), "alloc threshold flags");
-            CK(cudaMallocAsync((void **)&S.dir, (nd + 1) * 4, st), "alloc threshold directory");
+            CK(dev_alloc((void **)&S.flags, flag_words(S.nb) * 8, st), "alloc threshold flags");
+            CK(dev_alloc((void **)&S.dir, (nd + 1) * 4, st), "alloc threshold directory");
             const ThreshSeg seg{0, S.nb, 0, 0};
             CK(cudaMemcpyAsync(dseg, &seg, sizeof(seg), cudaMemcpyHostToDevice, st), "copy threshold segment");
         } else {
-            CK(cudaMallocAsync((void **)&S.thresh, tw * 8, st), "alloc thresholds");
+            CK(dev_alloc((void **)&S.thresh, std::max<uint64_t>(tw, 1) * 8, st), "alloc thresholds");
             CK(cudaMemsetAsync(S.thresh, 0, tw * 8, st), "clear thresholds");
         }
-        CK(cudaMallocAsync((void **)&S.z, (S.m / 64) * r * 8, st), "alloc table");
+        CK(dev_alloc((void **)&S.z, std::max<uint64_t>((S.m / 64) * r, 1) * 8, st), "alloc table");
         if (!bk[which]) {
             CK(ar.alloc(&bk[which], cur_n * 8), "alloc bumped keys");
             CK(ar.alloc(&bv[which], cur_n * vb), "alloc bumped values");
@@ -431,7 +489,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             // band reuses the per-bucket array)
             S.nflag = nflag;
             S.tfirst = 0;
-            CK(cudaMallocAsync((void **)&S.tbytes, std::max<uint64_t>(nflag, 1), st), "alloc thresholds");
+            CK(dev_alloc((void **)&S.tbytes, std::max<uint64_t>(nflag, 1), st), "alloc thresholds");
             CK(launch_thresh_compact(tex, dseg, blkseg, (uint32_t)nd, S.flags, S.dir, S.tbytes, st), "compact");
             h->launches += 1;
         }
@@ -448,7 +506,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         bool solved = false;
         for (uint32_t a = 0; a <= p.fallback_max_retries && !solved; ++a) {
             if (F.z) {
-                cudaFreeAsync(F.z, st);
+                dev_free_async(F.z, st);
                 F.z = nullptr;
             }
             F.m = fallback_slots(cur_n, p.fallback_slack, a);
@@ -472,7 +530,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
                 CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
             }
             CK(side.reuse(set), "order");
-            CK(cudaMallocAsync((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");
+            CK(dev_alloc((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");
             CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
             const LayerDesc L = make_desc(p, r, cur_n, F.m, F.sigma, 1, true, F.m);
             const int t0 = tm.mark();
@@ -693,7 +751,7 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
     };
     auto table_alloc = [&](size_t bytes, auto **d) -> cudaError_t {
         void *q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(bytes, 8), st);
+        cudaError_t e = dev_alloc(&q, std::max<size_t>(bytes, 8), st);
         if (e == cudaSuccess) store->ptrs.push_back(q);
         *d = static_cast<std::remove_reference_t<decltype(**d)> *>(q);
         return e;
@@ -1019,6 +1077,18 @@ int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n
     CK(launch_query(Q, vb, k, o, n, st), "query");
     if (!dout) CK(cudaMemcpyAsync(out, o, n * vb, cudaMemcpyDeviceToHost, st), "copy query output");
     CK(cudaStreamSynchronize(st), "query");
+    return BURR_OK;
+}
+
+int burr_set_allocator(burr_alloc_fn alloc, burr_free_fn free, void *ctx) {
+    if ((alloc == nullptr) != (free == nullptr)) return fail(BURR_ERR_INVALID, "alloc and free must both be set or both NULL");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_live.load() != 0)
+        return fail(BURR_ERR_INVALID, "%lld device blocks of the current allocator are still held",
+                    (long long)g_live.load());
+    g_hook.alloc = alloc;
+    g_hook.free = free;
+    g_hook.ctx = alloc ? ctx : nullptr;
     return BURR_OK;
 }
 

@@ -162,6 +162,14 @@ cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64
 // Record a message for burr_last_error() and return `code`.
 int set_error(int code, const char *msg);
 
+// Device memory of the library (the caller's allocator if set, else the
+// device's stream-ordered pool): allocation usable in stream order on st,
+// release after the work on st, and release of a handle's table (waits for
+// the device first).
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free_async(void *p, cudaStream_t st);
+void dev_free_sync(void *p);
+
 inline unsigned grid_for(uint64_t work, unsigned per_block, unsigned cap) {
     uint64_t g = (work + per_block - 1) / per_block;
     if (g < 1) g = 1;

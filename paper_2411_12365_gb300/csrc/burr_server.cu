@@ -222,10 +222,10 @@ int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
     uint64_t *dk = nullptr;
     uint8_t *dv = nullptr;
     if (N) {
-        if (cudaMallocAsync((void **)&dk, N * 8, st) != cudaSuccess ||
-            cudaMallocAsync((void **)&dv, N * vb, st) != cudaSuccess) {
+        if (burr::dev_alloc((void **)&dk, N * 8, st) != cudaSuccess ||
+            burr::dev_alloc((void **)&dv, N * vb, st) != cudaSuccess) {
             cudaGetLastError();
-            if (dk) cudaFreeAsync(dk, st);
+            if (dk) burr::dev_free_async(dk, st);
             return burr::set_error(BURR_ERR_OOM, "batch input allocation failed");
         }
         for (size_t j = 0; j < g.size(); ++j) {
@@ -234,8 +234,8 @@ int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
                     cudaSuccess ||
                 cudaMemcpyAsync(dv + offs[j] * vb, g[j]->tail(), g[j]->n * vb, cudaMemcpyHostToDevice, st) !=
                     cudaSuccess) {
-                cudaFreeAsync(dk, st);
-                cudaFreeAsync(dv, st);
+                burr::dev_free_async(dk, st);
+                burr::dev_free_async(dv, st);
                 return burr::set_error(BURR_ERR_CUDA, "batch input copy failed");
             }
         }
@@ -243,8 +243,8 @@ int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
     std::vector<burr_handle *> hs(g.size(), nullptr);
     const int rc = burr_build_batch(dk, dv, offs.data(), rs.data(), (uint32_t)g.size(), &S->params, st, hs.data());
     if (N) {
-        cudaFreeAsync(dk, st);
-        cudaFreeAsync(dv, st);
+        burr::dev_free_async(dk, st);
+        burr::dev_free_async(dv, st);
     }
     if (rc == BURR_OK)
         for (size_t j = 0; j < g.size(); ++j) g[j]->handle = hs[j];

@@ -69,3 +69,17 @@ def test_server_rejects_bad_config_without_touching_the_device(lib):
             burr.Server(budget, **kw)
         assert e.value.code == burr.ERR_INVALID
     assert C.sizeof(burr.ServerConfig) == 24 and C.sizeof(burr.ServerStats) == 96
+
+
+def test_allocator_hook_arguments_without_the_device(lib):
+    from paper_2411_12365_gb300 import burr
+    burr.load(os.path.join(ROOT, "paper_2411_12365_gb300", "_lib", "libburr.so"))
+    with pytest.raises(ValueError):
+        burr.set_allocator(alloc=lambda n, s: 0)
+    L = burr.load()
+    with pytest.raises(burr.BurrError):                       # one of the pair missing
+        burr._check(L.burr_set_allocator(burr._ALLOC_FN(lambda n, s, c: None), burr._FREE_FN(), None))
+    calls = []
+    burr.set_allocator(lambda n, s: calls.append(n) or 0, lambda p, s: None)   # nothing held: accepted
+    burr.set_allocator(None, None)
+    assert calls == []                                        # installing allocates nothing

@@ -1,0 +1,75 @@
+"""Device memory through the caller's allocator (burr_set_allocator).
+
+PyTorch's caching allocator backs every build, query and batched build; the
+results equal those of the built-in pool, the tables of a live handle sit in
+PyTorch's pool, the allocator cannot be changed while blocks are held, and
+every block comes back.
+"""
+import numpy as np
+import pytest
+
+from paper_2411_12365_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_12365_gb300 import burr  # noqa: E402
+
+
+def test_torch_caching_allocator_backs_the_library():
+    keys = I.keys_torch(300_000, "cuda", seed=77)
+    vals = I.values_torch(keys, 8)
+    offs = [0, 1000, 50_000, 300_000]
+    bp = dict(partition_slots=4096, min_partition_slots=4096, threshold_mode=burr.THRESH_1PLUS)
+    ref = burr.build(keys, vals, 8, partition_slots=8192)
+    ref_ex = ref.export()
+    ref.free()
+    refs_b = burr.build_batch(keys, vals, offs, [8, 8, 8], **bp)
+    ref_bex = [h.export() for h in refs_b]
+    del refs_b
+    torch.cuda.synchronize()
+
+    count = {"alloc": 0, "free": 0, "live": 0}
+    dev = torch.cuda.current_device()
+
+    def alloc(n, stream):
+        count["alloc"] += 1
+        count["live"] += 1
+        return torch.cuda.caching_allocator_alloc(n, dev, stream)
+
+    def free(ptr, stream):
+        count["free"] += 1
+        count["live"] -= 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    base = torch.cuda.memory_allocated()
+    burr.set_allocator(alloc, free)
+    handles = []
+    try:
+        h = burr.build(keys, vals, 8, partition_slots=8192)
+        handles.append(h)
+        assert h.export() == ref_ex
+        assert torch.cuda.memory_allocated() - base >= h.size_bytes() - 64   # tables in torch's pool
+        assert torch.equal(h.query(keys), vals)
+        out = h.query(keys.cpu().numpy().view(np.uint64))                     # host pointers: staged
+        assert np.array_equal(out, vals.cpu().numpy())
+        hs = burr.build_batch(keys, vals, offs, [8, 8, 8], **bp)
+        handles += hs
+        assert [x.export() for x in hs] == ref_bex
+        with pytest.raises(burr.BurrError):
+            burr.set_allocator(None, None)                                    # blocks still held
+        assert count["live"] > 0
+    finally:
+        for x in handles:
+            x.free()
+        handles.clear()
+        hs = None
+        torch.cuda.synchronize()
+    assert count["alloc"] > 0 and count["live"] == 0 and count["alloc"] == count["free"]
+    burr.set_allocator(None, None)
+    # the built-in pool again
+    h2 = burr.build(keys, vals, 8, partition_slots=8192)
+    assert h2.export() == ref_ex
