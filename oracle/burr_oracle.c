@@ -21,6 +21,8 @@
  *   - parallel construction: the equation system is cut into partitions and the
  *     first bucket after every cut bumps at least w-1 slots, so no kept equation
  *     overlaps a cut and partitions are independent             (Sec. 3, "Bumping")
+ *   - optional cut-point search: move each cut to a nearby bucket where the
+ *     cut bumps fewer keys or where more keys precede it     (Sec. 3, "Selecting Cut Points")
  *   - back-substitution                                         (Sec. 4, Fig. 7)
  *   - bumped keys go to the next layer; 4 layers, then a base case that cannot
  *     bump and is scaled up until it solves                     (Sec. 3, Sec. 4)
@@ -391,6 +393,55 @@ static uint32_t or_layer_eval(const uint64_t *z, uint32_t r, uint64_t s, uint64_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cut-point search (Sec. 3, "Selecting Cut Points").                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Cut j (1 <= j < K) is searched among the buckets b0, b0+1, ..., b0+R-1 with
+ * b0 = j*P/B and R = min(range, P/B) (READING: the paper gives only "the
+ * number of buckets to be searched"; searching forward from the nominal cut
+ * and never a whole partition keeps the cuts increasing).  For a cut at
+ * bucket b (slot c = b*B):
+ *   bumped(b) = keys with start in [c, c + w)   (cut away by the forced level)
+ *   prev(b)   = keys with start in [c - (w-1), c) (the w-1 slots before)
+ * minbump minimises bumped(b), maxprev maximises prev(b), diff minimises
+ * bumped(b) - prev(b); the first best candidate wins.  OR_CUT_NONE or
+ * range <= 1 gives c = j*P.
+ */
+int or_search_cuts(const uint64_t *keys, uint64_t n, uint64_t m, uint64_t sigma, uint32_t B, uint32_t w,
+                   uint64_t P, uint64_t K, uint32_t mode, uint32_t range, uint64_t *cuts)
+{
+    if (K < 2) return 0;
+    for (uint64_t j = 1; j < K; j++) cuts[j - 1] = j * P;
+    if (mode == OR_CUT_NONE || range <= 1) return 0;
+    uint64_t nb = or_num_buckets(m, w, B);
+    /* per bucket: keys at offsets < w, and keys at offsets >= B - (w - 1) */
+    uint64_t *lo = (uint64_t *)calloc(nb + 1, sizeof(uint64_t));
+    uint64_t *hi = (uint64_t *)calloc(nb + 1, sizeof(uint64_t));
+    if (!lo || !hi) { free(lo); free(hi); return OR_ENOMEM; }
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t s, c;
+        or_hash(keys[i], sigma, m, w, &s, &c);
+        uint32_t off = (uint32_t)(s % B);
+        if (off < w) lo[s / B]++;
+        if (off >= B - (w - 1)) hi[s / B]++;
+    }
+    uint64_t R = range < P / B ? range : P / B;
+    for (uint64_t j = 1; j < K; j++) {
+        uint64_t b0 = j * P / B, best_b = b0;
+        int64_t best = 0;
+        for (uint64_t b = b0; b < b0 + R && b < nb; b++) {
+            int64_t bumped = (int64_t)lo[b], prev = b > 0 ? (int64_t)hi[b - 1] : 0;
+            int64_t score = mode == OR_CUT_MINBUMP ? bumped : (mode == OR_CUT_MAXPREV ? -prev : bumped - prev);
+            if (b == b0 || score < best) { best = score; best_b = b; }
+        }
+        cuts[j - 1] = best_b * B;
+    }
+    free(lo); free(hi);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole structure.                                                          */
 /* ------------------------------------------------------------------------ */
 
@@ -406,6 +457,8 @@ void or_default_params(or_params *p)
     p->partition_slots = 65536;
     p->min_partition_slots = 4096;
     p->lower_partition_slots = 4096;
+    p->cut_search = OR_CUT_NONE;
+    p->cut_search_range = 50;
     p->seed = 0x5EED5EED5EED5EEDULL;
     p->fb_max_retries = 16;
     p->fb_slack = 0.1;
@@ -418,6 +471,7 @@ void or_free(or_struct *s)
         free(s->layer[l].thresh);
         free(s->layer[l].z);
         free(s->layer[l].texact);
+        free(s->layer[l].cuts);
     }
     memset(s, 0, sizeof(*s));
 }
@@ -439,6 +493,7 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         p->lower_partition_slots % p->B != 0 ||
         !(p->alpha > 0.0) || or_forced_code(p->levels, p->w) < 0 ||
         (p->threshold_mode != OR_THRESH_2BIT && p->threshold_mode != OR_THRESH_1PLUS) ||
+        p->cut_search > OR_CUT_DIFF ||
         (p->threshold_mode == OR_THRESH_1PLUS && p->B > 255))
         return OR_EINVAL;
     out->params = *p;
@@ -472,13 +527,19 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         L->part_slots = P;
         uint64_t ncuts = L->nparts ? L->nparts - 1 : 0;
         uint64_t *cuts = (uint64_t *)malloc(sizeof(uint64_t) * (ncuts ? ncuts : 1));
-        for (uint64_t j = 0; j < ncuts; j++) cuts[j] = (j + 1) * P;
+        if (cuts && or_search_cuts(ck, cn, L->m, or_layer_seed(p->seed, l), p->B, p->w, P, L->nparts,
+                                   p->cut_search, p->cut_search_range, cuts) != 0) {
+            free(cuts);
+            cuts = NULL;
+        }
+        L->cuts = (uint64_t *)malloc(sizeof(uint64_t) * (ncuts ? ncuts : 1));
+        if (L->cuts && cuts) memcpy(L->cuts, cuts, sizeof(uint64_t) * ncuts);
         const int onep = p->threshold_mode == OR_THRESH_1PLUS;
         if (onep) L->texact = (uint8_t *)calloc(L->nbuckets + 1, 1);
         else L->thresh = (uint64_t *)calloc((L->nbuckets + 31) / 32 + 1, sizeof(uint64_t));
         L->z = (uint64_t *)calloc((L->m / 64) * p->r + 1, sizeof(uint64_t));
         uint64_t nb = 0;
-        if (!cuts || !(onep ? (void *)L->texact : (void *)L->thresh) || !L->z) status = OR_ENOMEM;
+        if (!cuts || !L->cuts || !(onep ? (void *)L->texact : (void *)L->thresh) || !L->z) status = OR_ENOMEM;
         else
             status = or_build_layer_mode(ck, cv, cn, p->r, L->m,
                                          or_layer_seed(p->seed, l), p->levels, p->B, p->w,

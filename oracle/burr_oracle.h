@@ -15,6 +15,11 @@
 #define OR_THRESH_2BIT 0u   /* four threshold levels, 2 bits per bucket */
 #define OR_THRESH_1PLUS 1u  /* exact threshold; 1 bit per bucket + the bumping buckets' thresholds */
 
+#define OR_CUT_NONE 0u      /* cut j at j*P */
+#define OR_CUT_MINBUMP 1u   /* fewest keys bumped by the cut itself */
+#define OR_CUT_MAXPREV 2u   /* most keys in the w-1 slots before the cut */
+#define OR_CUT_DIFF 3u      /* least (bumped by the cut) - (keys in the w-1 slots before) */
+
 typedef struct {
     uint32_t r;                     /* value bits, 1..32 */
     uint32_t w;                     /* ribbon width, 64 */
@@ -31,10 +36,13 @@ typedef struct {
     uint32_t threshold_mode;        /* OR_THRESH_2BIT or OR_THRESH_1PLUS */
     uint32_t pad;
     uint64_t lower_partition_slots; /* P of layers >= 1 (0 = partition_slots) */
+    uint32_t cut_search;            /* OR_CUT_* */
+    uint32_t cut_search_range;      /* buckets searched from each nominal cut */
 } or_params;
 
 typedef struct {
     uint64_t n, m, seed_index, nbuckets, nparts, part_slots, nbumped;
+    uint64_t *cuts;                 /* nparts-1 cut start slots used */
     uint64_t *thresh;               /* 2-bit mode: ceil(nbuckets/32) words of 2-bit codes */
     uint64_t *z;                    /* (m/64)*r words, interleaved bit planes */
     uint8_t *texact;                /* 1+-bit mode: exact threshold of every bucket, 0..B */
@@ -79,6 +87,8 @@ int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                         uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
                         uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
                         or_stats *st);
+int or_search_cuts(const uint64_t *keys, uint64_t n, uint64_t m, uint64_t sigma, uint32_t B, uint32_t w,
+                   uint64_t P, uint64_t K, uint32_t mode, uint32_t range, uint64_t *cuts);
 void or_default_params(or_params *p);
 int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
              const or_params *p, or_struct *out, or_stats *st);

@@ -27,6 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "libburr_oracle.so")
 MAX_LAYERS = 8
 EINVAL, ENOMEM, UNSOLVABLE, FAIL = -1, -2, -3, -4
 THRESH_2BIT, THRESH_1PLUS = 0, 1
+CUT_NONE, CUT_MINBUMP, CUT_MAXPREV, CUT_DIFF = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -52,14 +53,15 @@ class Params(C.Structure):
         ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64),
         ("seed", C.c_uint64), ("fb_slack", C.c_double),
         ("cut_P", C.c_uint64 * MAX_LAYERS), ("threshold_mode", C.c_uint32), ("pad", C.c_uint32),
-        ("lower_partition_slots", C.c_uint64),
+        ("lower_partition_slots", C.c_uint64), ("cut_search", C.c_uint32), ("cut_search_range", C.c_uint32),
     ]
 
 
 class Layer(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in
                 ("n", "m", "seed_index", "nbuckets", "nparts", "part_slots", "nbumped")] + [
-        ("thresh", C.POINTER(C.c_uint64)), ("z", C.POINTER(C.c_uint64)), ("texact", C.POINTER(C.c_uint8))]
+        ("cuts", C.POINTER(C.c_uint64)), ("thresh", C.POINTER(C.c_uint64)), ("z", C.POINTER(C.c_uint64)),
+        ("texact", C.POINTER(C.c_uint8))]
 
 
 class Struct(C.Structure):
@@ -96,6 +98,8 @@ def lib():
             L.or_build_layer_mode.restype = C.c_int
             L.or_build_layer_mode.argtypes = [p, p, u64, u32, u64, u64, p, u32, u32, p, u64, C.c_int,
                                               u32, p, p, p, p, p, C.POINTER(u64), C.POINTER(Stats)]
+            L.or_search_cuts.restype = C.c_int
+            L.or_search_cuts.argtypes = [p, u64, u64, u64, u32, u32, u64, u64, u32, u32, p]
             L.or_struct_size.restype = u64; L.or_struct_size.argtypes = []
             L.or_params_size.restype = u64; L.or_params_size.argtypes = []
             L.or_layer_size.restype = u64; L.or_layer_size.argtypes = []
@@ -240,11 +244,14 @@ class OracleStruct:
         nz = (L.m // 64) * r
         thresh = (np.ctypeslib.as_array(L.thresh, shape=(nw,)).copy()
                   if (nw and bool(L.thresh) and l != "fallback") else np.zeros(0, np.uint64))
+        nc = max(int(L.nparts) - 1, 0)
+        cuts = (np.ctypeslib.as_array(L.cuts, shape=(nc,)).copy()
+                if (nc and bool(L.cuts) and l != "fallback") else np.zeros(0, np.uint64))
         texact = (np.ctypeslib.as_array(L.texact, shape=(L.nbuckets,)).copy()
                   if (L.nbuckets and bool(L.texact) and l != "fallback") else np.zeros(0, np.uint8))
         z = np.ctypeslib.as_array(L.z, shape=(nz,)).copy() if nz else np.zeros(0, np.uint64)
         return dict(n=L.n, m=L.m, seed_index=L.seed_index, nbuckets=L.nbuckets,
-                    nparts=L.nparts, nbumped=L.nbumped, thresh=thresh, z=z, texact=texact)
+                    nparts=L.nparts, nbumped=L.nbumped, thresh=thresh, z=z, texact=texact, cuts=cuts)
 
     @property
     def fb_attempt(self):
@@ -269,3 +276,12 @@ class OracleStruct:
 
 def build(keys, vals, **params) -> OracleStruct:
     return OracleStruct(keys, vals, default_params(**params))
+
+
+def search_cuts(keys, m, sigma, P, K, mode, search_range, B=128, w=64) -> np.ndarray:
+    """Cut start slots (K-1) chosen by the cut-point search of one layer."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.zeros(max(K - 1, 1), dtype=np.uint64)
+    rc = lib().or_search_cuts(_ptr(keys), len(keys), m, sigma, B, w, P, K, mode, search_range, _ptr(out))
+    assert rc == 0
+    return out[:max(K - 1, 0)]

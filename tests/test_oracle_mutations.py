@@ -34,6 +34,8 @@ MUTATIONS = {
     "exact_threshold_not_stored": ("texact[b] = (uint8_t)t;", "texact[b] = (uint8_t)(t ? 1 : 0);"),
     "exact_forced_threshold_too_small": ("const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w :",
                                          "const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w - 1 :"),
+    "cut_search_prev_window_too_wide": ("if (off >= B - (w - 1)) hi[s / B]++;", "if (off >= B - w) hi[s / B]++;"),
+    "cut_search_keeps_last_best": ("if (b == b0 || score < best)", "if (b == b0 || score <= best)"),
 }
 
 
@@ -48,7 +50,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-I", os.path.join(ROOT, "oracle"),
                            "-o", str(lib), str(mut), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(lib))
-    pins = ["tests/test_oracle_hash.py", "tests/test_oracle_bruteforce.py", "tests/test_oracle_invariants.py"]
+    pins = ["tests/test_oracle_hash.py", "tests/test_oracle_bruteforce.py", "tests/test_oracle_invariants.py",
+            "tests/test_oracle_cut_search.py"]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
