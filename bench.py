@@ -44,6 +44,9 @@ def args_():
     ap.add_argument("--r", type=int, default=8)
     ap.add_argument("--partition-slots", type=int, default=65536)
     ap.add_argument("--lower-partition-slots", type=int, default=4096)
+    ap.add_argument("--cut-search", default="none", choices=["none", "minbump", "maxprev", "diff"],
+                    help="cut-point search (Sec. 3) over --cut-search-range buckets from each nominal cut")
+    ap.add_argument("--cut-search-range", type=int, default=50)
     ap.add_argument("--thresholds", default="2bit", choices=["2bit", "1plus"],
                     help="threshold storage: 2-bit levels or 1+-bit (bit per bucket + exact thresholds)")
     ap.add_argument("--min-partition-slots", type=int, default=4096)
@@ -171,7 +174,8 @@ def max_over_ranks(pg, x: float) -> float:
     return float(t.item())
 
 
-def oracle_sample(n_s: int, r: int, P: int, minP: int = 4096, lowP: int = 4096, mode: int = 0):
+def oracle_sample(n_s: int, r: int, P: int, minP: int = 4096, lowP: int = 4096, mode: int = 0, cut: int = 0,
+                  cut_range: int = 50):
     """Serial CPU oracle: build + query of n_s keys; returns (seconds, n_s)."""
     import numpy as np
 
@@ -182,7 +186,7 @@ def oracle_sample(n_s: int, r: int, P: int, minP: int = 4096, lowP: int = 4096, 
     q = np.concatenate([k[: n_s // 2], I.keys_np(n_s - n_s // 2, offset=n_s)])
     t0 = time.perf_counter()
     s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=minP, lower_partition_slots=lowP,
-                threshold_mode=mode)
+                threshold_mode=mode, cut_search=cut, cut_search_range=cut_range)
     out = s.query(q)
     dt = time.perf_counter() - t0
     assert s.ok and np.array_equal(out[: n_s // 2], v[: n_s // 2])
@@ -197,10 +201,12 @@ def run_reference(a, ws, rank, pg):
     O.build_lib()
     n_s = a.ref_sample
     for _ in range(a.warmup):
-        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a))
+        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a),
+                      cmode(a), a.cut_search_range)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a))
+        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a),
+                      cmode(a), a.cut_search_range)
     dt = (time.perf_counter() - t0) / a.steps
     value = n_s / dt / 1e6
     line = {
@@ -219,8 +225,14 @@ def tmode(a) -> int:
     return 1 if a.thresholds == "1plus" else 0
 
 
+def cmode(a) -> int:
+    return ["none", "minbump", "maxprev", "diff"].index(a.cut_search)
+
+
 def workload_config(a):
     tdesc = "1+-bit thresholds" if a.thresholds == "1plus" else "2-bit thresholds"
+    if a.cut_search != "none":
+        tdesc += f", {a.cut_search} cut search over {a.cut_search_range} buckets"
     return {"workload": f"{a.keys} uniform-random 64-bit keys, r={a.r}, w=64, {tdesc}, "
                         f"partition size {a.partition_slots} slots in layer 0 and {a.lower_partition_slots} "
                         f"in deeper layers, plain build + {a.keys} queries "
@@ -228,7 +240,7 @@ def workload_config(a):
             "n_keys": a.keys, "queries": a.keys, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
             "partition_slots": a.partition_slots, "lower_partition_slots": a.lower_partition_slots,
             "min_partition_slots": a.min_partition_slots, "load_factor": 1.015, "layers": 4,
-            "thresholds": a.thresholds,
+            "thresholds": a.thresholds, "cut_search": a.cut_search, "cut_search_range": a.cut_search_range,
             "l2_flush": "inputs larger than L2 (keys 8n bytes)", "parallelism": "one independent structure per GPU"}
 
 
@@ -508,7 +520,7 @@ def main():
     qout = torch.empty(n, dtype=burr.value_torch_dtype(r), device=dev)
     params = burr.default_params(partition_slots=P, min_partition_slots=a.min_partition_slots,
                                  lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a),
-                                 flags=burr.FLAG_TIMING)
+                                 cut_search=cmode(a), cut_search_range=a.cut_search_range, flags=burr.FLAG_TIMING)
     torch.cuda.synchronize()
 
     stats_acc = []
@@ -598,7 +610,8 @@ def main():
         ho = torch.empty(n, dtype=qout.dtype).pin_memory()
         hk_np, hv_np, hq_np, ho_np = hk.numpy(), hv.numpy(), hq.numpy(), ho.numpy()
         p2 = burr.default_params(partition_slots=P, min_partition_slots=a.min_partition_slots,
-                                 lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a))
+                                 lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a),
+                                 cut_search=cmode(a), cut_search_range=a.cut_search_range)
 
         def e2e_step():
             h = burr.build(hk_np, hv_np, r, params=p2)
@@ -619,7 +632,8 @@ def main():
                        "h2d_bytes_per_step": n * 8 + n * vb + n * 8, "d2h_bytes_per_step": n * vb}
 
     if not a.no_cpu and rank == 0:
-        dt = oracle_sample(a.cpu_sample, r, P, a.min_partition_slots, a.lower_partition_slots, tmode(a))
+        dt = oracle_sample(a.cpu_sample, r, P, a.min_partition_slots, a.lower_partition_slots, tmode(a),
+                      cmode(a), a.cut_search_range)
         line["cpu_baseline"] = {"value": a.cpu_sample / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"serial C oracle: build + query of {a.cpu_sample} keys "
                                           f"(same r, P, load; {dt:.1f} s)"}

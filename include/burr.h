@@ -39,8 +39,12 @@
  *                deeper layers (the paper's minimum buckets per thread, Sec. 3:
  *                deep layers are small, so their partitions are short);
  *                K = 1 if m < max(P, min_partition_slots), else floor(m/P);
- *                cut j at start slot j*P, the last partition takes the rest;
- *                partition j owns slots [j*P + 64, (j+1)*P + 64)
+ *                cut j at start slot c_j = j*P, the last partition takes the
+ *                rest; partition j owns slots [c_j + 64, c_{j+1} + 64)
+ *   cut search   (Sec. 3, optional) c_j is the bucket among the first
+ *                min(range, P/B) buckets from j*P that minimises: keys at its
+ *                offsets < 64 (minbump), minus keys in the 63 slots before it
+ *                (maxprev), or their difference (diff); first best wins
  *   table layout per 64-slot block, r 64-bit words; bit k of slot s is bit
  *                s%64 of word (s/64)*r + k
  *   thresholds   2-bit codes, 32 per 64-bit word, bucket b in bits
@@ -79,6 +83,10 @@ extern "C" {
 
 #define BURR_THRESH_2BIT 0u       /* four threshold levels, 2 bits per bucket */
 #define BURR_THRESH_1PLUS 1u      /* 1+-bit: a bit per bucket, exact thresholds of bumping buckets */
+#define BURR_CUT_NONE 0u          /* cut j of a layer at start slot j*P */
+#define BURR_CUT_MINBUMP 1u       /* cut search: fewest keys bumped by the cut itself */
+#define BURR_CUT_MAXPREV 2u       /* cut search: most keys in the w-1 slots before the cut */
+#define BURR_CUT_DIFF 3u          /* cut search: least (bumped by the cut) - (keys before it) */
 #define BURR_MAX_LAYERS 8
 #define BURR_FLAG_TIMING 1u       /* record per-stage device times (burr_stats) */
 
@@ -100,6 +108,8 @@ typedef struct {
     uint32_t fallback_max_retries;  /* base-case retries, each with 10% more slots (16) */
     uint32_t flags;                 /* BURR_FLAG_* */
     uint64_t lower_partition_slots; /* P of bumping layers >= 1, a multiple of B; 0 = partition_slots (4096) */
+    uint32_t cut_search;            /* BURR_CUT_* (BURR_CUT_NONE) */
+    uint32_t cut_search_range;      /* buckets searched from each nominal cut (50) */
 } burr_params;
 
 /* Per-build statistics. */

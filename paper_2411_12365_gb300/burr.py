@@ -20,6 +20,7 @@ ERR_INVALID, ERR_OOM, ERR_UNSOLVABLE, ERR_TIMEOUT, ERR_CUDA, ERR_INTERNAL = -1, 
 MAX_LAYERS = 8
 FLAG_TIMING = 1
 THRESH_2BIT, THRESH_1PLUS = 0, 1
+CUT_NONE, CUT_MINBUMP, CUT_MAXPREV, CUT_DIFF = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -37,7 +38,7 @@ class Params(C.Structure):
         ("layers", C.c_uint32), ("levels", C.c_uint32 * 4), ("load_factor", C.c_double),
         ("partition_slots", C.c_uint64), ("min_partition_slots", C.c_uint64), ("seed", C.c_uint64),
         ("fallback_slack", C.c_double), ("fallback_max_retries", C.c_uint32), ("flags", C.c_uint32),
-        ("lower_partition_slots", C.c_uint64),
+        ("lower_partition_slots", C.c_uint64), ("cut_search", C.c_uint32), ("cut_search_range", C.c_uint32),
     ]
 
 

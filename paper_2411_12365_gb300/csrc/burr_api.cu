@@ -97,6 +97,7 @@ int validate(const burr_params &p, uint32_t r) {
         return fail(BURR_ERR_INVALID, "partition_slots must be a positive multiple of bucket_slots");
     if (p.lower_partition_slots % p.bucket_slots != 0)
         return fail(BURR_ERR_INVALID, "lower_partition_slots must be a multiple of bucket_slots");
+    if (p.cut_search > BURR_CUT_DIFF) return fail(BURR_ERR_INVALID, "cut_search must be a BURR_CUT_* value");
     if (!(p.fallback_slack >= 0.0) || !std::isfinite(p.fallback_slack))
         return fail(BURR_ERR_INVALID, "fallback_slack must be >= 0");
     return BURR_OK;
@@ -453,7 +454,13 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(ar.alloc(&bv[which], cur_n * vb), "alloc bumped values");
         }
         CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
-        const LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false, layer_partition_slots(p, l));
+        LayerDesc L = make_desc(p, r, cur_n, S.m, S.sigma, S.K, false, layer_partition_slots(p, l));
+        const bool search = p.cut_search != BURR_CUT_NONE && S.K > 1;
+        if (search) {
+            uint32_t *dc;
+            CK(ar.alloc((void **)&dc, (S.K + 1) * 4), "alloc cuts");
+            L.cuts = dc;
+        }
         const int set = (int)(l & 1);
         if (cgcap[set] < S.m) {           // second band set, sized by the first layer that uses it
             CK(ar.alloc(&cgs[set], S.m * 8), "alloc band");
@@ -464,6 +471,12 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         CK(side.reuse(set), "order");
         tev[l][0] = tm.mark();
         CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+        if (search) {
+            CK(launch_cut_search(L, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search, p.cut_search_range,
+                                 const_cast<uint32_t *>(L.cuts), st),
+               "cut search");
+            h->launches += 1;
+        }
         tev[l][1] = tm.mark();
         CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
                        S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
@@ -774,6 +787,20 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         int rc = batch_tables(p, r, offsets, n, who, l, nullptr, T);
         if (rc) return rc;
         if ((rc = ensure(T))) return rc;
+        // cut search: a table of partition starts per structure with cuts
+        const bool search = p.cut_search != BURR_CUT_NONE;
+        if (search) {
+            uint64_t ncut = 0;
+            for (const StructDesc &D : T.sd) ncut += D.L.K > 1 ? D.L.K + 1 : 0;
+            uint32_t *dc = nullptr;
+            CK(ar.alloc((void **)&dc, std::max<uint64_t>(ncut, 1) * 4), "alloc cuts");
+            ncut = 0;
+            for (StructDesc &D : T.sd) {
+                if (D.L.K < 2) continue;
+                D.L.cuts = dc + ncut;
+                ncut += D.L.K + 1;
+            }
+        }
         BatchView v;
         if ((rc = view(T, v))) return rc;
         uint64_t *th = nullptr, *z, *tflags = nullptr;
@@ -804,6 +831,12 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         const int w = (int)(l & 1);
         const int t0 = tm.mark();
         CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
+        if (search) {
+            CK(launch_cut_search(none, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search,
+                                 p.cut_search_range, nullptr, st, &v),
+               "cut search");
+            for (auto *h : hs) h->launches += 1;
+        }
         const int t1 = tm.mark();
         CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
                        (uint64_t *)bk[w], bv2[w], bcount, err, st, &v), "band");
@@ -940,6 +973,8 @@ int burr_default_params(burr_params *p) {
     p->partition_slots = 65536;
     p->min_partition_slots = 4096;
     p->lower_partition_slots = 4096;
+    p->cut_search = BURR_CUT_NONE;
+    p->cut_search_range = 50;
     p->seed = 0x5EED5EED5EED5EEDull;
     p->fallback_slack = 0.1;
     p->fallback_max_retries = 16;

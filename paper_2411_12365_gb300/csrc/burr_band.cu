@@ -362,10 +362,10 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     const uint64_t part = x.part;
     BandWarpSmem &S = smem[warp];
 
-    const uint64_t b0 = part * L.P / L.B;
-    const uint64_t b1 = (part == L.K - 1) ? L.nb : (part + 1) * L.P / L.B;
-    const uint64_t own_lo = part == 0 ? 0 : part * L.P + kW;
-    const uint64_t own_hi = part == L.K - 1 ? L.m : (part + 1) * L.P + kW;
+    const uint64_t b0 = part_bucket(L, part);
+    const uint64_t b1 = part_bucket(L, part + 1);
+    const uint64_t own_lo = part_own_lo(L, part);
+    const uint64_t own_hi = part_own_hi(L, part);
 
     for (int i = lane; i < kRing; i += 32) {
         S.ring[i].c = 0;
@@ -488,8 +488,8 @@ k_backsub(LayerDesc L0, const uint64_t *__restrict__ Cg0, const V *__restrict__ 
         part = gp;
     }
     if (part >= L.K) return;
-    const uint64_t own_lo = part == 0 ? 0 : part * L.P + kW;
-    const uint64_t own_hi = part == L.K - 1 ? L.m : (part + 1) * L.P + kW;
+    const uint64_t own_lo = part_own_lo(L, part);
+    const uint64_t own_hi = part_own_hi(L, part);
     const uint64_t blo = own_lo >> 6, bhi = own_hi >> 6;
     if (bhi <= blo) return;
     uint64_t T = 0;

@@ -58,7 +58,20 @@ struct LayerDesc {
     uint32_t vmask;      // (1 << r) - 1
     uint32_t mode;       // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
     uint32_t pad;
+    const uint32_t *cuts;  // device: first bucket of each partition, [K] = nb; nullptr: partition j at j*P
 };
+
+// First bucket of partition j (j <= K) and the slots it owns.
+__host__ __device__ inline uint64_t part_bucket(const LayerDesc &L, uint64_t j) {
+    if (L.cuts) return L.cuts[j];
+    return j >= L.K ? L.nb : j * L.P / L.B;
+}
+__host__ __device__ inline uint64_t part_own_lo(const LayerDesc &L, uint64_t j) {
+    return j == 0 ? 0 : part_bucket(L, j) * L.B + 64;
+}
+__host__ __device__ inline uint64_t part_own_hi(const LayerDesc &L, uint64_t j) {
+    return j + 1 >= L.K ? L.m : part_bucket(L, j + 1) * L.B + 64;
+}
 
 // One structure's layer inside a batched build: its layer descriptor and
 // where its data sits in the layer-wide arrays shared by the batch.
@@ -158,6 +171,13 @@ cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *ke
 
 cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64_t range,
                         uint32_t *start, uint64_t *coeff, cudaStream_t st);
+
+// Cut-point search (BURR_CUT_*): the first bucket of every partition of the
+// layer, cuts[0..K] (cuts[K] = nb), from the bucket-sorted keys.  With a
+// batch view, every structure's table sits at its L.cuts.
+cudaError_t launch_cut_search(const LayerDesc &L, const uint64_t *sorted_keys, const uint32_t *bucket_start,
+                              uint32_t mode, uint32_t range, uint32_t *cuts, cudaStream_t st,
+                              const BatchView *bv = nullptr);
 
 // Record a message for burr_last_error() and return `code`.
 int set_error(int code, const char *msg);

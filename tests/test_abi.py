@@ -43,17 +43,18 @@ def test_default_params_layout(lib):
     from paper_2411_12365_gb300 import burr
     burr.load(os.path.join(ROOT, "paper_2411_12365_gb300", "_lib", "libburr.so"))
     p = burr.default_params()
-    assert C.sizeof(burr.Params) == 88
+    assert C.sizeof(burr.Params) == 96
     assert (p.ribbon_width, p.bucket_slots, p.layers, list(p.levels)) == (64, 128, 4, [0, 32, 64, 128])
     assert p.load_factor == 1.015 and p.partition_slots == 65536 and p.fallback_max_retries == 16
     assert p.lower_partition_slots == 4096 and p.min_partition_slots == 4096
+    assert p.cut_search == burr.CUT_NONE and p.cut_search_range == 50
     # the oracle's defaults are the same workload
     from oracle import oracle as O
     q = O.default_params()
     assert (q.alpha, q.partition_slots, q.min_partition_slots, q.seed, q.layers, q.fb_slack,
-            q.lower_partition_slots) == \
+            q.lower_partition_slots, q.cut_search, q.cut_search_range) == \
         (p.load_factor, p.partition_slots, p.min_partition_slots, p.seed, p.layers, p.fallback_slack,
-         p.lower_partition_slots)
+         p.lower_partition_slots, p.cut_search, p.cut_search_range)
 
 
 def test_strerror(lib):

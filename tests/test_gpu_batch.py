@@ -113,3 +113,18 @@ def test_batch_1plus_thresholds():
         ref = O.build(k_np[a:b], v_np[a:b] & ((1 << rs[s]) - 1), r=rs[s], partition_slots=2048,
                       min_partition_slots=2048, threshold_mode=O.THRESH_1PLUS)
         assert hs[s].export() == ref.export(), describe_difference(hs[s].export(), ref.export())
+
+
+def test_batch_cut_search():
+    rng = np.random.default_rng(6)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(100), np.log(200_000), size=25))]
+    rs = [int(x) for x in rng.choice([2, 8], size=len(sizes))]
+    hs, keys, vals, offs = _check_batch(sizes, rs, partition_slots=2048, min_partition_slots=2048,
+                                        cut_search=burr.CUT_MAXPREV)
+    k_np = keys.cpu().numpy().view(np.uint64)
+    v_np = vals.cpu().numpy().astype(np.uint32)
+    big = int(np.argmax(sizes))
+    a, b = int(offs[big]), int(offs[big + 1])
+    ref = O.build(k_np[a:b], v_np[a:b] & ((1 << rs[big]) - 1), r=rs[big], partition_slots=2048,
+                  min_partition_slots=2048, cut_search=O.CUT_MAXPREV)
+    assert hs[big].export() == ref.export(), describe_difference(hs[big].export(), ref.export())

@@ -246,3 +246,32 @@ def test_1plus_10m_whole_structure_and_space():
     assert np.array_equal(_vals_np(h1.query(neg)), ref.query(_u64(neg)))
     h2 = burr.build(keys, vals, r)
     assert h1.size_bytes() < h2.size_bytes()               # the point of 1+-bit thresholds
+
+
+# Cut-point search (Sec. 3): cuts moved by the library's search kernel give
+# the same structure as the oracle's search
+
+CUT_CASES = [
+    (300_000, dict(partition_slots=8192)),
+    (200_003, dict(partition_slots=2048, min_partition_slots=2048, cut_search_range=7)),
+    (90_000, dict(partition_slots=1024, lower_partition_slots=512, min_partition_slots=512,
+                  threshold_mode=burr.THRESH_1PLUS)),
+    (120_000, dict(partition_slots=384, lower_partition_slots=256, min_partition_slots=0, load_factor=1.3)),
+]
+
+
+@pytest.mark.parametrize("mode", [burr.CUT_MINBUMP, burr.CUT_MAXPREV, burr.CUT_DIFF])
+@pytest.mark.parametrize("n,params", CUT_CASES)
+def test_cut_search_matches_oracle(mode, n, params):
+    _check_build(n, 8, cut_search=mode, **params)
+
+
+def test_cut_search_10m_whole_structure():
+    n, r = 10_000_000, 8
+    keys, vals = _kv(n, r, seed=5)
+    h = burr.build(keys, vals, r, cut_search=burr.CUT_DIFF)
+    ref = O.build(_u64(keys), _vals_np(vals), r=r, cut_search=O.CUT_DIFF)
+    got, want = h.export(), ref.export()
+    assert got == want, describe_difference(got, want)
+    plain = burr.build(keys, vals, r)
+    assert h.size_bytes() <= plain.size_bytes()
