@@ -1100,17 +1100,49 @@ int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n
     }
     keep_pool_memory();
     Arena ar(st);
-    const uint64_t *k = keys;
-    void *o = out;
-    if (!dk) {
-        void *d;
-        CK(ar.alloc(&d, n * 8), "alloc query keys");
-        CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy query keys");
-        k = (const uint64_t *)d;
+    constexpr uint64_t kChunk = 1ull << 22;   // keys per pipelined chunk
+    if (n <= 2 * kChunk) {
+        const uint64_t *k = keys;
+        void *o = out;
+        if (!dk) {
+            void *d;
+            CK(ar.alloc(&d, n * 8), "alloc query keys");
+            CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy query keys");
+            k = (const uint64_t *)d;
+        }
+        if (!dout) CK(ar.alloc(&o, n * vb), "alloc query output");
+        CK(launch_query(Q, vb, k, o, n, st), "query");
+        if (!dout) CK(cudaMemcpyAsync(out, o, n * vb, cudaMemcpyDeviceToHost, st), "copy query output");
+        CK(cudaStreamSynchronize(st), "query");
+        return BURR_OK;
     }
-    if (!dout) CK(ar.alloc(&o, n * vb), "alloc query output");
-    CK(launch_query(Q, vb, k, o, n, st), "query");
-    if (!dout) CK(cudaMemcpyAsync(out, o, n * vb, cudaMemcpyDeviceToHost, st), "copy query output");
+    // Large batches through host memory: chunks alternate between two streams,
+    // so the copies of one chunk overlap the query kernel of the other (with
+    // page-locked host memory; pageable copies are staged by the driver).
+    SideStream side(st);
+    CK(side.init(), "query stream");
+    void *kb[2] = {nullptr, nullptr}, *ob[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2; ++i) {
+        if (!dk) CK(ar.alloc(&kb[i], kChunk * 8), "alloc query keys");
+        if (!dout) CK(ar.alloc(&ob[i], kChunk * vb), "alloc query output");
+    }
+    CK(side.order(st, side.side, 2), "order");   // the second stream starts after the allocations
+    for (uint64_t c = 0, i = 0; c < n; c += kChunk, ++i) {
+        const uint64_t cnt = std::min(kChunk, n - c);
+        const int b = (int)(i & 1);
+        cudaStream_t s = b ? side.side : st;
+        const uint64_t *k = keys + c;
+        void *o = (uint8_t *)out + c * vb;
+        if (!dk) {
+            CK(cudaMemcpyAsync(kb[b], keys + c, cnt * 8, cudaMemcpyHostToDevice, s), "copy query keys");
+            k = (const uint64_t *)kb[b];
+        }
+        if (!dout) o = ob[b];
+        CK(launch_query(Q, vb, k, o, cnt, s), "query");
+        if (!dout) CK(cudaMemcpyAsync((uint8_t *)out + c * vb, ob[b], cnt * vb, cudaMemcpyDeviceToHost, s),
+                      "copy query output");
+    }
+    CK(side.order(side.side, st, 3), "order");
     CK(cudaStreamSynchronize(st), "query");
     return BURR_OK;
 }

@@ -275,3 +275,20 @@ def test_cut_search_10m_whole_structure():
     assert got == want, describe_difference(got, want)
     plain = burr.build(keys, vals, r)
     assert h.size_bytes() <= plain.size_bytes()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_large_host_query_is_pipelined_and_exact(pinned):
+    # more than two 2^22-key chunks through host memory: chunks alternate
+    # between two streams; results equal the device-pointer query
+    keys, vals = _kv(1 << 20, 8, seed=21)
+    h = burr.build(keys, vals, 8)
+    q = torch.cat([keys, I.keys_torch(9_000_000, DEV, seed=21, offset=1 << 20)])
+    want = h.query(q).cpu().numpy()
+    qh = q.cpu()
+    out = torch.empty(q.numel(), dtype=torch.uint8)
+    if pinned:
+        qh, out = qh.pin_memory(), out.pin_memory()
+    got = h.query(qh.numpy().view(np.uint64), out=out.numpy())
+    assert np.array_equal(got, want)
+    assert np.array_equal(got[: 1 << 20], vals.cpu().numpy())
