@@ -21,15 +21,16 @@
 //     rows is independent whenever a superset is, so each probe inserts the
 //     rows of [mid, t_ok) on top of those already kept and either keeps them
 //     (t_ok = mid) or rolls them back (t_fail = mid).
-//   * A set is inserted as a stream.  Each lane takes the next row of the set
-//     (a shared-memory counter) and eliminates it on its own, with no
-//     per-step vote or barrier: one step is one 128-bit compare-and-swap on
-//     the ring slot of the row's leading bit, which either claims the slot if
-//     it is empty (row and right-hand side stored in one atomic write) or
-//     returns the stored row and right-hand side to XOR with.  This is a
-//     sequential insertion in claim order: every slot a row eliminated
+//   * A set is inserted as a stream: the 32 lanes eliminate one row each and
+//     take their steps in lockstep.  A step is one 128-bit compare-and-swap
+//     on the ring slot of the row's leading bit, which either claims the
+//     slot if it is empty (row and right-hand side stored in one atomic
+//     write) or returns the stored row and right-hand side to XOR with.  This
+//     is a sequential insertion in claim order: every slot a row eliminated
 //     against was occupied when read and stays so, and a row is stored only
-//     on a slot that was still empty.
+//     on a slot that was still empty.  Lanes whose row was stored take the
+//     next rows of the set, and the stored slots are listed for a rollback,
+//     by ballot and prefix count; a dependent row ends the set at once.
 //   * Rows are staged per bucket in shared memory in ascending offset order
 //     (a counting sort on the 7-bit offset), so each threshold band is a
 //     contiguous range and rows that run through the dense overflow of the
@@ -64,9 +65,7 @@ struct BandWarpSmem {
     uint32_t ry[kStage];           // staged right-hand sides
     uint8_t ro[kStage];            // staged offsets
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
-    uint32_t next;                 // next staged row to hand out
     uint32_t ncommit;              // entries of clist
-    uint32_t flag;                 // 1 = dependent set, 2 = ring overflow
 };
 
 template <typename V>
@@ -182,19 +181,15 @@ __device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, u
                  : "memory");
 }
 
-// Each lane eliminates its own rows; a step is one 128-bit CAS that claims an
-// empty slot or returns the stored (row, right-hand side).
 // Stream staged rows [lo, hi) (index range) into the band; stored ring
-// indices are appended to S.clist (S.ncommit).  Returns kOk, kDependent or
-// kOverflow; nothing is rolled back here.  Every lane eliminates its own row
-// (one slot_cas per step) and takes the next row when its row is stored.
+// indices are appended to S.clist (from S.ncommit).  Returns kOk, kDependent
+// or kOverflow; nothing is rolled back here.  Every lane takes one step per
+// iteration; stores, the commit list and the hand-out of the next rows go by
+// ballot and prefix count, with no shared atomics besides the swaps.
 __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
-    if (lane == 0) {
-        S.next = lo + 32u;
-        S.flag = 0;
-    }
-    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t next = lo + 32u, nc = S.ncommit;
     uint32_t idx = lo + (uint32_t)lane;
     bool has = idx < hi;
     unsigned long long cur = 0, y = 0;
@@ -204,42 +199,46 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         y = kYValid | S.ry[idx];
         pos = bB + S.ro[idx];
     }
-    volatile uint32_t *vflag = &S.flag;
-    while (has) {
-        unsigned long long oc, oy;
-        slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
-        if (oc == 0ull) {
-            S.clist[atomicAdd(&S.ncommit, 1u)] = (uint16_t)(pos & kRingMask);
-            has = false;
-            if (*vflag == 0u) {
-                idx = atomicAdd(&S.next, 1u);
-                if (idx < hi) {
-                    cur = S.rc[idx];
-                    y = kYValid | S.ry[idx];
-                    pos = bB + S.ro[idx];
-                    has = true;
-                }
+    int result = kOk;
+    while (__any_sync(kFull, has)) {
+        unsigned long long oc = 0, oy = 0;
+        if (has) slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
+        const bool stored = has && oc == 0ull;
+        bool dep = false, ovf = false;
+        if (has && !stored) {
+            cur ^= oc;
+            y ^= oy & ~kYValid;
+            dep = cur == 0ull;
+            const uint32_t lo32 = (uint32_t)cur;
+            const int tz = dep ? 0 : (lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(cur >> 32)));
+            cur >>= tz;
+            pos += (uint32_t)tz;
+            ovf = !dep && pos - bB >= (uint32_t)kRing;
+        }
+        const unsigned sm = __ballot_sync(kFull, stored);
+        const uint32_t rank = (uint32_t)__popc(sm & lt);
+        if (stored) {
+            S.clist[nc + rank] = (uint16_t)(pos & kRingMask);
+            idx = next + rank;
+            has = idx < hi;
+            if (has) {
+                cur = S.rc[idx];
+                y = kYValid | S.ry[idx];
+                pos = bB + S.ro[idx];
             }
-            continue;
         }
-        cur ^= oc;
-        y ^= oy & ~kYValid;
-        if (cur == 0ull) {
-            atomicOr(&S.flag, 1u);
-            break;
-        }
-        const uint32_t lo32 = (uint32_t)cur;
-        const int tz = lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(cur >> 32));
-        cur >>= tz;
-        pos += (uint32_t)tz;
-        if (pos - bB >= (uint32_t)kRing) {
-            atomicOr(&S.flag, 2u);
+        nc += (uint32_t)__popc(sm);
+        next += (uint32_t)__popc(sm);
+        const unsigned bad = __ballot_sync(kFull, dep || ovf);
+        if (bad) {
+            result = __ballot_sync(kFull, ovf) ? kOverflow : kDependent;
             break;
         }
     }
     __syncwarp();
-    const uint32_t f = S.flag;
-    return (f & 2u) ? kOverflow : ((f & 1u) ? kDependent : kOk);
+    if (lane == 0) S.ncommit = nc;
+    __syncwarp();
+    return result;
 }
 
 // Insert the rows of bucket [rs, re) whose offset lies in [olo, ohi) as one
