@@ -69,7 +69,8 @@ def _check_build(n, r, seed=I.KEY_SEED, **params):
     keys, vals = _kv(n, r, seed=seed)
     h = burr.build(keys, vals, r, **params)
     got = h.export()
-    names = {"load_factor": "alpha", "fallback_max_retries": "fb_max_retries", "fallback_slack": "fb_slack"}
+    names = {"load_factor": "alpha", "fallback_max_retries": "fb_max_retries", "fallback_slack": "fb_slack",
+             "bucket_slots": "B"}
     ref = O.build(_u64(keys), _vals_np(vals), r=r, **{names.get(k, k): v for k, v in params.items()})
     assert ref.ok
     want = ref.export()
@@ -292,3 +293,18 @@ def test_large_host_query_is_pipelined_and_exact(pinned):
     got = h.query(qh.numpy().view(np.uint64), out=out.numpy())
     assert np.array_equal(got, want)
     assert np.array_equal(got[: 1 << 20], vals.cpu().numpy())
+
+
+
+# Buckets of 64 start slots (the forced level after a cut is the whole bucket)
+
+@pytest.mark.parametrize("n,r,params", [
+    (100_000, 8, dict(partition_slots=4096, min_partition_slots=4096)),
+    (70_001, 3, dict(partition_slots=1024, min_partition_slots=0, levels=(0, 8, 40, 64))),
+    (50_000, 16, dict(threshold_mode=burr.THRESH_1PLUS, partition_slots=2048, min_partition_slots=2048)),
+    (80_000, 8, dict(cut_search=burr.CUT_DIFF, partition_slots=2048, min_partition_slots=2048)),
+])
+def test_64_slot_buckets_match_oracle(n, r, params):
+    params = dict(params)
+    params.setdefault("levels", (0, 16, 32, 64))
+    _check_build(n, r, bucket_slots=64, **params)
