@@ -129,7 +129,7 @@ size_t sort_batch_scratch_bytes(uint64_t nkeys, uint64_t ngroups, uint32_t vbyte
 cudaError_t launch_sort_batch(const BatchView &bv, uint32_t vbytes, const uint64_t *keys, const void *vals,
                               uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
                               cudaStream_t st);
-constexpr uint32_t kSortTile = 4096;      // keys per tile of the batched sort
+constexpr uint32_t kSortTile = 2048;      // keys per tile of the batched sort
 constexpr uint32_t kMaxGroupsPerStruct = 1024;
 
 // Query descriptor: every layer of a handle.

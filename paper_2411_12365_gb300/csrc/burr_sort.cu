@@ -8,7 +8,7 @@
 //
 //   * groups of 64 buckets (about 8k keys) are the unit of the last pass;
 //   * one or two scatter passes bring the keys into group order.  Each pass
-//     works in tiles of 4096 keys: a shared-memory histogram and scan order
+//     works in tiles of 2048 keys: a shared-memory histogram and scan order
 //     the tile by digit in shared memory, one global atomic per (tile, digit)
 //     reserves the output range, and the tile is written out as contiguous
 //     runs per digit (coalesced stores, not scattered 8-byte writes);
@@ -29,8 +29,8 @@ constexpr int kGroupShift = 6;                  // 64 buckets per group
 constexpr uint32_t kGroupBuckets = 1u << kGroupShift;
 constexpr int kHistThreads = 256;
 constexpr int kTileThreads = 256;
-constexpr int kTileItems = 16;
-constexpr int kTile = kTileThreads * kTileItems; // 4096 keys per tile
+constexpr int kTileItems = 8;
+constexpr int kTile = kTileThreads * kTileItems; // 2048 keys per tile (63 registers: 4 CTAs per SM)
 constexpr uint32_t kMaxDigits = 1024;           // digits of one scatter pass
 constexpr int kGroupThreads = 512;
 constexpr uint32_t kGroupCap = 12288;           // keys a group may hold to be sorted in shared memory
@@ -365,7 +365,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, 0, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false><<<grid_for(n, kTile, sms * 3), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, 0, P.D1, S.u1, S.keys, (V *)S.vals);
         goff = S.o1;
         gk = S.keys;
@@ -379,7 +379,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, P.d2, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false><<<grid_for(n, kTile, sms * 3), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
         uint64_t per64 = (sms * 4ull + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
         if (per64 > 8) per64 = 8;
