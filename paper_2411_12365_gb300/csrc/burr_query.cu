@@ -30,6 +30,84 @@ __device__ __forceinline__ uint32_t eval_window(const uint64_t *__restrict__ z, 
     return v;
 }
 
+// The 2r table words around slot s (blocks s/64 and s/64 + 1), loaded before
+// the threshold is known so that both reads are in flight together; R is the
+// value width fixed at compile time.
+template <int R>
+struct Window {
+    uint64_t w0[R], w1[R];
+};
+
+template <int R>
+__device__ __forceinline__ void load_window(const uint64_t *__restrict__ z, uint32_t s, Window<R> &w) {
+    const uint64_t *p = z + (uint64_t)(s >> 6) * R;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        w.w0[k] = __ldg(p + k);
+        w.w1[k] = __ldg(p + R + k);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t eval_loaded(const Window<R> &w, uint32_t s, uint64_t c) {
+    const uint32_t o = s & 63u;
+    uint32_t v = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const uint64_t win = o ? (w.w0[k] >> o) | (w.w1[k] << (64 - o)) : w.w0[k];
+        v |= (uint32_t)(__popcll(win & c) & 1) << k;
+    }
+    return v;
+}
+
+// Threshold t of bucket b of bumping layer l: keys with offset < t are bumped.
+__device__ __forceinline__ uint32_t threshold_of(const QueryDesc &Q, uint32_t l, uint32_t b) {
+    if (Q.mode == BURR_THRESH_1PLUS) {
+        // flag bit; a flagged bucket's threshold sits at its rank
+        const uint64_t *fl = Q.flags[l];
+        const uint64_t w = __ldg(fl + (b >> 6));
+        if (!((w >> (b & 63u)) & 1ull)) return 0;
+        uint32_t rank = __ldg(Q.dir[l] + (b >> 9));
+        for (uint32_t k = (b >> 9) << 3; k < (b >> 6); ++k) rank += (uint32_t)__popcll(__ldg(fl + k));
+        rank += (uint32_t)__popcll(w & ((1ull << (b & 63u)) - 1ull));
+        return __ldg(Q.tbytes[l] + rank);
+    }
+    return Q.levels[(uint32_t)(__ldg(Q.thresh[l] + (b >> 5)) >> (2 * (b & 31))) & 3u];
+}
+
+// Query kernel for a value width R known at compile time: the table window
+// of a layer is loaded together with its threshold.
+template <typename V, int R>
+__global__ void __launch_bounds__(kQThreads)
+k_query_r(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t log2B = 31 - __clz(Q.B);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = keys[i];
+        uint32_t v = 0;
+        uint32_t l = 0;
+        for (; l < Q.layers; ++l) {
+            const uint64_t m = Q.m[l];
+            if (m == 0) break;
+            const uint64_t h = mix64(key ^ Q.sigma[l]);
+            const uint32_t s = (uint32_t)__umul64hi(h, m - kW + 1);
+            Window<R> w;
+            load_window<R>(Q.z[l], s, w);
+            if ((s & (Q.B - 1)) < threshold_of(Q, l, s >> log2B)) continue;   // bumped: next layer
+            v = eval_loaded<R>(w, s, mix64(h + Q.sigma[l]) | 1ull);
+            break;
+        }
+        if (l == Q.layers && Q.m[l] != 0) {                    // base case
+            const uint64_t h = mix64(key ^ Q.sigma[l]);
+            const uint32_t s = (uint32_t)__umul64hi(h, Q.m[l] - kW + 1);
+            Window<R> w;
+            load_window<R>(Q.z[l], s, w);
+            v = eval_loaded<R>(w, s, mix64(h + Q.sigma[l]) | 1ull);
+        }
+        out[i] = (V)v;
+    }
+}
+
 template <typename V>
 __global__ void __launch_bounds__(kQThreads)
 k_query(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uint64_t n) {
@@ -46,22 +124,7 @@ k_query(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uin
             const uint32_t s = (uint32_t)__umul64hi(h, m - kW + 1);
             const uint32_t b = s >> log2B;
             const uint32_t off = s & (Q.B - 1);
-            uint32_t t;
-            if (Q.mode == BURR_THRESH_1PLUS) {
-                // flag bit; a flagged bucket's threshold sits at its rank
-                const uint64_t *fl = Q.flags[l];
-                const uint64_t w = __ldg(fl + (b >> 6));
-                if ((w >> (b & 63u)) & 1ull) {
-                    uint32_t rank = __ldg(Q.dir[l] + (b >> 9));
-                    for (uint32_t k = (b >> 9) << 3; k < (b >> 6); ++k) rank += (uint32_t)__popcll(__ldg(fl + k));
-                    rank += (uint32_t)__popcll(w & ((1ull << (b & 63u)) - 1ull));
-                    t = __ldg(Q.tbytes[l] + rank);
-                } else {
-                    t = 0;
-                }
-            } else {
-                t = Q.levels[(uint32_t)(__ldg(Q.thresh[l] + (b >> 5)) >> (2 * (b & 31))) & 3u];
-            }
+            const uint32_t t = threshold_of(Q, l, b);
             if (off < t) continue;                             // bumped: next layer
             v = eval_window(Q.z[l], Q.r, s, mix64(h + Q.sigma[l]) | 1ull);
             break;
@@ -93,6 +156,19 @@ cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *ke
                          cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const unsigned grid = grid_for(n, kQThreads, 152u * 64u);
+    // common widths: the window is loaded together with the threshold
+    if (Q.r == 8 && vbytes == 1) {
+        k_query_r<uint8_t, 8><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
+        return cudaGetLastError();
+    }
+    if (Q.r == 1 && vbytes == 1) {
+        k_query_r<uint8_t, 1><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
+        return cudaGetLastError();
+    }
+    if (Q.r == 16 && vbytes == 2) {
+        k_query_r<uint16_t, 16><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n);
+        return cudaGetLastError();
+    }
     switch (vbytes) {
     case 1: k_query<uint8_t><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n); break;
     case 2: k_query<uint16_t><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n); break;
