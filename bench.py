@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="burr", choices=["burr", "reference"])
     ap.add_argument("--keys", type=int, default=100_000_000, help="keys per structure")
@@ -536,8 +536,9 @@ def main():
 
     for _ in range(a.warmup):
         step()
-    # correctness of the timed configuration
-    assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
+    # correctness of the timed configuration (again after the timed steps)
+    if a.warmup:
+        assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
     stats_acc.clear()
     launches[0] = 0
     torch.cuda.synchronize()
@@ -553,6 +554,7 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
     barrier(pg)
+    assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
     ms = ev0.elapsed_time(ev1) / a.steps
     ms = max_over_ranks(pg, ms)
     value = ws * n / (ms / 1e3) / 1e6
@@ -576,10 +578,26 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = band_bytes / (band0 / 1e3) / 1e9
     traffic = ncu_traffic(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
-    # space overhead (bits of tables + thresholds over r*n)
-    bits = sum(st0["layer_m"][l] * r + 2 * ((st0["layer_m"][l] - 64 + 128) // 128 if st0["layer_m"][l] else 0)
-               for l in range(layers)) + st0["layer_m"][layers] * r
-    overhead = bits / (r * n) - 1
+    # space overhead: bits of the device tables (Z, thresholds) over r*n
+    overhead = (st0["table_bytes"] - 64) * 8 / (r * n) - 1
+    # whole-stage rooflines against compulsory bytes (SURVEY 8(d) model):
+    # build: per layer-l key read (key, value) and one partition-order round
+    # trip, bumped keys written into the next layer, the table written once;
+    # query: the key and the output, per visited layer one threshold sector and
+    # the 2r-word table window in 32-byte sectors
+    ln, lm = st0["layer_n"], st0["layer_m"]
+    build_bytes = (sum(ln[:layers + 1]) * 3 * (8 + vb) + sum(ln[1:layers + 1]) * (8 + vb)
+                   + sum(lm[:layers + 1]) * r // 8)
+    visits = sum(ln[:layers + 1]) / max(ln[0], 1)
+    query_bytes = n * (8 + vb) + n * visits * (32 + -(-2 * r * 8 // 32) * 32)
+    query_ms = ms - build_ms
+    stage_roofline = {
+        "peak_gbs": peak, "peak_kind": peak_kind,
+        "build": {"compulsory_bytes": build_bytes, "achieved_gbs": build_bytes / (build_ms / 1e3) / 1e9,
+                  "frac": build_bytes / (build_ms / 1e3) / 1e9 / peak},
+        "query": {"compulsory_bytes": query_bytes, "achieved_gbs": query_bytes / (query_ms / 1e3) / 1e9,
+                  "frac": query_bytes / (query_ms / 1e3) / 1e9 / peak},
+    }
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -592,6 +610,7 @@ def main():
             "stage_ms_per_layer": [[round(x, 4) for x in s] for s in st0["stage_ms"]],
             "layer_n": st0["layer_n"], "layer_m": st0["layer_m"], "layer_parts": st0["layer_parts"],
             "space_overhead": overhead,
+            "roofline_by_stage": stage_roofline,
             "paper_cpu_context": "67.8 Mkeys/s construction, 1e8 keys, 64 threads on EPYC 7551P (Fig. 7)",
         },
         "roofline": {"bound": "hbm", "kernel": "k_band (layer 0)", "achieved": achieved, "peak": peak,
