@@ -227,6 +227,22 @@ int burr_size_bytes(const burr_handle *h, uint64_t *bytes);
  */
 int burr_export(const burr_handle *h, void *host_buf, uint64_t *len);
 
+/*
+ * Load a structure from the export format above (written by burr_export, or by
+ * any writer of the same format): the device tables are allocated and filled
+ * and the handle answers queries exactly as the exported structure did.
+ * Checkpoint/resume of built structures (the paper has no counterpart).
+ *   host_buf, len  the export bytes (host memory, read only);
+ *   stream         cudaStream_t of the copies (the call returns when they are done);
+ *   out            receives a handle owned by the library until burr_free.
+ * The whole buffer is checked before anything is allocated: magic, version,
+ * parameters, layer sizes (n, slots, buckets, bumped keys chaining from layer
+ * to layer), flag and threshold counts, and the exact length.  Errors:
+ * BURR_ERR_INVALID (malformed buffer), BURR_ERR_OOM, BURR_ERR_CUDA.  Build
+ * statistics (stage times) of an imported handle are zero.
+ */
+int burr_import(const void *host_buf, uint64_t len, void *stream, burr_handle **out);
+
 int burr_stats(const burr_handle *h, burr_stats_t *st);
 
 /* Release the handle and its device memory (NULL is ignored). */

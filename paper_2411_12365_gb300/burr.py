@@ -69,7 +69,7 @@ EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query
             "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
             "burr_stage_sort", "burr_stage_sort_noalloc", "burr_server_create", "burr_server_submit_build",
             "burr_server_submit_query", "burr_server_wait", "burr_server_handle", "burr_server_release",
-            "burr_server_stats", "burr_server_destroy", "burr_set_allocator"]
+            "burr_server_stats", "burr_server_destroy", "burr_set_allocator", "burr_import"]
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -136,6 +136,8 @@ def load(path: str | None = None):
         L.burr_server_destroy.restype = None
         L.burr_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, p]
         L.burr_set_allocator.restype = i
+        L.burr_import.argtypes = [p, u64, p, C.POINTER(p)]
+        L.burr_import.restype = i
         _lib = L
         return L
 
@@ -257,6 +259,17 @@ def build(keys, values, r: int, params: Params | None = None, stream=None, **kw)
     n = int(kk.numel() if hasattr(kk, "numel") else kk.size)
     out = C.c_void_p()
     _check(load().burr_build(kp, vp, n, r, C.byref(params), st, C.byref(out)))
+    return Handle(out.value, r)
+
+
+def import_export(buf: bytes, stream=None) -> Handle:
+    """burr_import: a device-resident structure from export bytes."""
+    import struct
+    raw = bytes(buf)
+    out = C.c_void_p()
+    b = (C.c_uint8 * len(raw)).from_buffer_copy(raw) if raw else (C.c_uint8 * 1)()
+    _check(load().burr_import(b, len(raw), _stream_value(stream), C.byref(out)))
+    r = struct.unpack_from("<I", raw, 8)[0]
     return Handle(out.value, r)
 
 

@@ -361,6 +361,7 @@ struct SideStream {
 
 int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params &p,
                cudaStream_t st, burr_handle *h) {
+    TraceRange trace("burr_build");
     const uint32_t vb = value_bytes(r);
     keep_pool_memory();
     Arena ar(st);
@@ -427,11 +428,14 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     const void *cur_v = dvals;
     uint64_t cur_n = n;
     int which = 0;
+    static const char *kLayerNames[] = {"burr layer 0", "burr layer 1", "burr layer 2", "burr layer 3",
+                                        "burr layer 4", "burr layer 5", "burr layer 6", "burr layer 7"};
     for (uint32_t l = 0; l < p.layers; ++l) {
         LayerStore &S = h->L[l];
         S.n = cur_n;
         S.seed_index = l;
         if (cur_n == 0) continue;
+        TraceRange layer_trace(kLayerNames[l]);
         S.m = layer_slots(cur_n, p.load_factor);
         if (S.m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "layer %u needs %llu slots (>= 2^32)", l,
                                              (unsigned long long)S.m);
@@ -516,6 +520,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     LayerStore &F = h->L[p.layers];
     F.n = cur_n;
     if (cur_n > 0) {
+        TraceRange base_trace("burr base case");
         bool solved = false;
         for (uint32_t a = 0; a <= p.fallback_max_retries && !solved; ++a) {
             if (F.z) {
@@ -680,6 +685,7 @@ cudaError_t upload(Arena &ar, const std::vector<X> &v, X **d, cudaStream_t st) {
 int build_batch_impl(const uint64_t *keys, const void *values, const std::vector<uint64_t> &offsets,
                      const std::vector<uint32_t> &r, const burr_params &p, cudaStream_t st,
                      std::vector<burr_handle *> &hs, const std::shared_ptr<BatchStorage> &store) {
+    TraceRange trace("burr_build_batch");
     const uint32_t S = (uint32_t)r.size();
     uint32_t rmax = 1;
     for (uint32_t x : r) rmax = std::max(rmax, x);
@@ -1070,6 +1076,7 @@ int burr_build_batch(const uint64_t *keys, const void *values, const uint64_t *o
 }
 
 int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n, void *stream) {
+    TraceRange trace("burr_query");
     if (!h) return fail(BURR_ERR_INVALID, "handle is NULL");
     if (n == 0) return BURR_OK;
     if (!keys || !out) return fail(BURR_ERR_INVALID, "keys/out are NULL");
@@ -1275,6 +1282,185 @@ int burr_stats(const burr_handle *h, burr_stats_t *st) {
     burr_size_bytes(h, &b);
     st->table_bytes = b;
     st->kernel_launches = h->launches;
+    return BURR_OK;
+}
+
+namespace {
+
+// Little-endian reader over the export buffer that refuses to run past its end.
+struct Reader {
+    const uint8_t *p, *end;
+    bool ok = true;
+    uint32_t u32() {
+        uint32_t v = 0;
+        if (end - p < 4) ok = false;
+        else memcpy(&v, p, 4), p += 4;
+        return v;
+    }
+    uint64_t u64() {
+        uint64_t v = 0;
+        if (end - p < 8) ok = false;
+        else memcpy(&v, p, 8), p += 8;
+        return v;
+    }
+    const uint8_t *bytes(uint64_t n) {
+        if ((uint64_t)(end - p) < n) {
+            ok = false;
+            return nullptr;
+        }
+        const uint8_t *q = p;
+        p += n;
+        return q;
+    }
+};
+
+int upload_table(void **d, const void *src, uint64_t bytes, cudaStream_t st) {
+    CK(dev_alloc(d, std::max<uint64_t>(bytes, 8), st), "alloc imported table");
+    if (bytes) CK(cudaMemcpyAsync(*d, src, bytes, cudaMemcpyHostToDevice, st), "copy imported table");
+    return BURR_OK;
+}
+
+// Parse and check an export; with h == nullptr only the checks run.
+int import_into(const uint8_t *buf, uint64_t len, cudaStream_t st, burr_handle *h) {
+    Reader R{buf, buf + len};
+    if (R.u32() != 0x52525542u) return fail(BURR_ERR_INVALID, "not a BuRR export (magic)");
+    const uint32_t version = R.u32();
+    if (version != 1 && version != 2) return fail(BURR_ERR_INVALID, "unknown export version %u", version);
+    burr_params p;
+    burr_default_params(&p);
+    const uint32_t r = R.u32();
+    p.ribbon_width = R.u32();
+    p.bucket_slots = R.u32();
+    p.layers = R.u32();
+    for (int i = 0; i < 4; ++i) p.levels[i] = R.u32();
+    p.seed = R.u64();
+    const uint64_t abits = R.u64();
+    memcpy(&p.load_factor, &abits, 8);
+    const uint64_t n = R.u64();
+    p.partition_slots = R.u64();
+    p.threshold_mode = version == 2 ? BURR_THRESH_1PLUS : BURR_THRESH_2BIT;
+    if (!R.ok) return fail(BURR_ERR_INVALID, "export header truncated");
+    if (p.layers > BURR_MAX_LAYERS) return fail(BURR_ERR_INVALID, "export has %u layers", p.layers);
+    if (int rc = validate(p, r)) return rc;
+    uint64_t ln[BURR_MAX_LAYERS + 1], lm[BURR_MAX_LAYERS + 1], lk[BURR_MAX_LAYERS + 1], lb[BURR_MAX_LAYERS + 1],
+        lbump[BURR_MAX_LAYERS + 1];
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        ln[l] = R.u64();
+        lm[l] = R.u64();
+        lk[l] = R.u64();
+        lb[l] = R.u64();
+        lbump[l] = R.u64();
+    }
+    const uint64_t fn = R.u64(), fm = R.u64(), fseed = R.u64(), fatt = R.u64();
+    if (!R.ok) return fail(BURR_ERR_INVALID, "export layer table truncated");
+    uint64_t cur = n;
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        if (ln[l] != cur || lm[l] % 64 || lm[l] >= (1ull << 32) || lb[l] != num_buckets(lm[l], p.bucket_slots) ||
+            lbump[l] > ln[l] || (ln[l] == 0) != (lm[l] == 0))
+            return fail(BURR_ERR_INVALID, "export layer %u sizes are inconsistent", l);
+        cur = lbump[l];
+    }
+    if (fn != cur || fm % 64 || fm >= (1ull << 32) || (fn == 0) != (fm == 0) || fseed != p.layers + fatt)
+        return fail(BURR_ERR_INVALID, "export base-case sizes are inconsistent");
+    if (h) {
+        h->p = p;
+        h->r = r;
+        h->vbytes = value_bytes(r);
+        h->n = n;
+        h->fb_attempt = (uint32_t)fatt;
+    }
+    for (uint32_t l = 0; l < p.layers; ++l) {
+        LayerStore *S = h ? &h->L[l] : nullptr;
+        const uint64_t nb = lb[l];
+        if (S) {
+            S->n = ln[l];
+            S->m = lm[l];
+            S->nb = nb;
+            S->K = lk[l];
+            S->nbumped = lbump[l];
+            S->seed_index = l;
+            S->sigma = layer_seed(p.seed, l);
+        }
+        if (version == 2) {
+            const uint64_t fw = flag_words(nb), nd = dir_blocks(nb);
+            const uint8_t *fl = R.bytes(fw * 8);
+            const uint64_t cnt = R.u64();
+            const uint8_t *tb = R.bytes(8 * ((cnt + 7) / 8));
+            if (!R.ok) return fail(BURR_ERR_INVALID, "export thresholds of layer %u truncated", l);
+            // the rank directory is derived: flagged buckets before each 512-bucket block
+            std::vector<uint64_t> words(fw);
+            if (fw) memcpy(words.data(), fl, fw * 8);
+            std::vector<uint32_t> dir(nd + 1, 0);
+            uint64_t run = 0;
+            for (uint64_t w = 0; w < fw; ++w) {
+                if (w % 8 == 0) dir[w / 8] = (uint32_t)run;
+                run += (uint64_t)__builtin_popcountll(words[w]);
+            }
+            dir[nd] = (uint32_t)run;
+            if (run != cnt) return fail(BURR_ERR_INVALID, "export layer %u: %llu flags, %llu thresholds", l,
+                                        (unsigned long long)run, (unsigned long long)cnt);
+            if (fw && (nb % 64) && (words[fw - 1] >> (nb % 64)))
+                return fail(BURR_ERR_INVALID, "export layer %u flags past the last bucket", l);
+            for (uint64_t i = 0; i < cnt; ++i)
+                if (tb[i] == 0 || tb[i] > p.bucket_slots)
+                    return fail(BURR_ERR_INVALID, "export layer %u: threshold out of range", l);
+            if (S) {
+                if (int rc = upload_table((void **)&S->flags, words.data(), fw * 8, st)) return rc;
+                if (int rc = upload_table((void **)&S->dir, dir.data(), (nd + 1) * 4, st)) return rc;
+                if (int rc = upload_table((void **)&S->tbytes, tb, cnt, st)) return rc;
+                S->nflag = cnt;
+                S->tfirst = 0;
+            }
+        } else {
+            const uint64_t tw = (nb + 31) / 32;
+            const uint8_t *th = R.bytes(tw * 8);
+            if (!R.ok) return fail(BURR_ERR_INVALID, "export thresholds of layer %u truncated", l);
+            if (S)
+                if (int rc = upload_table((void **)&S->thresh, th, tw * 8, st)) return rc;
+        }
+        const uint64_t zw = (lm[l] / 64) * r;
+        const uint8_t *z = R.bytes(zw * 8);
+        if (!R.ok) return fail(BURR_ERR_INVALID, "export table of layer %u truncated", l);
+        if (S)
+            if (int rc = upload_table((void **)&S->z, z, zw * 8, st)) return rc;
+    }
+    const uint64_t zw = (fm / 64) * r;
+    const uint8_t *z = R.bytes(zw * 8);
+    if (!R.ok) return fail(BURR_ERR_INVALID, "export base-case table truncated");
+    if (R.p != R.end) return fail(BURR_ERR_INVALID, "export has %llu trailing bytes", (unsigned long long)(R.end - R.p));
+    if (h) {
+        LayerStore &F = h->L[p.layers];
+        F.n = fn;
+        F.m = fm;
+        F.nb = num_buckets(fm, p.bucket_slots);
+        F.K = fm ? 1 : 0;
+        F.seed_index = fseed;
+        F.sigma = layer_seed(p.seed, fseed);
+        if (int rc = upload_table((void **)&F.z, z, zw * 8, st)) return rc;
+    }
+    return BURR_OK;
+}
+
+}  // namespace
+
+int burr_import(const void *host_buf, uint64_t len, void *stream, burr_handle **out) {
+    if (!host_buf || !out) return fail(BURR_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    // every check runs before anything is allocated
+    if (int rc = import_into((const uint8_t *)host_buf, len, nullptr, nullptr)) return rc;
+    auto *h = new (std::nothrow) burr_handle();
+    if (!h) return fail(BURR_ERR_OOM, "host allocation");
+    cudaStream_t st = (cudaStream_t)stream;
+    TraceRange trace("burr_import");
+    keep_pool_memory();
+    int rc = import_into((const uint8_t *)host_buf, len, st, h);
+    if (rc == BURR_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? BURR_OK : fail(BURR_ERR_CUDA, "import");
+    if (rc) {
+        free_layers(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
     return BURR_OK;
 }
 

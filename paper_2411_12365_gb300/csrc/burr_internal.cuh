@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "burr.h"
 
 namespace burr {
@@ -181,6 +183,14 @@ cudaError_t launch_cut_search(const LayerDesc &L, const uint64_t *sorted_keys, c
 
 // Record a message for burr_last_error() and return `code`.
 int set_error(int code, const char *msg);
+
+// A named range on the host timeline for profilers (NVTX, header-only).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Device memory of the library (the caller's allocator if set, else the
 // device's stream-ordered pool): allocation usable in stream order on st,

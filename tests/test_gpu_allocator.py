@@ -73,3 +73,60 @@ def test_torch_caching_allocator_backs_the_library():
     # the built-in pool again
     h2 = burr.build(keys, vals, 8, partition_slots=8192)
     assert h2.export() == ref_ex
+    h2.free()
+
+
+@pytest.mark.parametrize("which", ["first", "middle", "last"])
+@pytest.mark.parametrize("kind", ["plain", "batch", "1plus"])
+def test_allocation_failure_is_clean(which, kind):
+    # host-side fault injection: the caller's allocator refuses one request;
+    # the call fails with BURR_ERR_OOM and every block it got is given back
+    keys = I.keys_torch(200_000, "cuda", seed=5)
+    vals = I.values_torch(keys, 8)
+    dev = torch.cuda.current_device()
+
+    def run():
+        if kind == "plain":
+            return [burr.build(keys, vals, 8, partition_slots=8192)]
+        if kind == "1plus":
+            return [burr.build(keys, vals, 8, threshold_mode=burr.THRESH_1PLUS)]
+        return burr.build_batch(keys, vals, [0, 70_000, 200_000], [8, 8], partition_slots=4096,
+                                min_partition_slots=4096)
+
+    count = {"alloc": 0, "free": 0, "fail_at": 0}
+
+    def alloc(n, stream):
+        count["alloc"] += 1
+        if count["alloc"] == count["fail_at"]:
+            return 0
+        return torch.cuda.caching_allocator_alloc(n, dev, stream)
+
+    def free(ptr, stream):
+        count["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    burr.set_allocator(alloc, free)
+    try:
+        hs = run()                                  # count the allocations of one call
+        total = count["alloc"]
+        for h in hs:
+            h.free()
+        del hs
+        torch.cuda.synchronize()
+        assert count["free"] == total
+        count.update(alloc=0, free=0, fail_at={"first": 1, "middle": total // 2, "last": total}[which])
+        code = None
+        try:
+            run()
+        except burr.BurrError as err:
+            code = err.code
+        assert code == burr.ERR_OOM
+        torch.cuda.synchronize()
+        assert count["free"] == count["alloc"] - 1  # all but the refused request came back
+    finally:
+        burr.set_allocator(None, None)
+    hs = run()                                      # the library works normally afterwards
+    if kind != "batch":
+        assert torch.equal(hs[0].query(keys[:1000]), vals[:1000])
+    for h in hs:
+        h.free()
