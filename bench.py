@@ -580,7 +580,7 @@ def main():
     traffic = ncu_traffic(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
     # space overhead: bits of the device tables (Z, thresholds) over r*n
     overhead = (st0["table_bytes"] - 64) * 8 / (r * n) - 1
-    # whole-stage rooflines against compulsory bytes (SURVEY 8(d) model):
+    # whole-stage rooflines against compulsory bytes:
     # build: per layer-l key read (key, value) and one partition-order round
     # trip, bumped keys written into the next layer, the table written once;
     # query: the key and the output, per visited layer one threshold sector and
