@@ -25,7 +25,9 @@
 //     take their steps in lockstep.  A step is one 128-bit compare-and-swap
 //     on the ring slot of the row's leading bit, which either claims the
 //     slot if it is empty (row and right-hand side stored in one atomic
-//     write) or returns the stored row and right-hand side to XOR with.  This
+//     write) or returns the stored row and right-hand side to XOR with.  Plain
+//     reads of the next three slots are in flight beside the swap, and the
+//     elimination goes on through those that hold stored rows.  This
 //     is a sequential insertion in claim order: every slot a row eliminated
 //     against was occupied when read and stays so, and a row is stored only
 //     on a slot that was still empty.  Lanes whose row was stored take the
@@ -181,11 +183,43 @@ __device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, u
                  : "memory");
 }
 
+// Plain 128-bit read of a ring slot.  A slot goes from empty to its final
+// contents once per set (one atomic write), so a read that sees a nonzero row
+// and a valid right-hand side has seen a stored equation that stays; any
+// other result (empty, or a torn read of a slot being written) is treated as
+// "not known to be occupied".
+__device__ __forceinline__ void slot_load(const RingSlot *slot, unsigned long long &c, unsigned long long &y) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c), "=l"(y) : "r"(addr) : "memory");
+}
+
+// Index of the lowest set bit of a nonzero 64-bit word.
+__device__ __forceinline__ int ctz64(unsigned long long v) {
+    const uint32_t lo32 = (uint32_t)v;
+    return lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(v >> 32));
+}
+
+// Ring slots read ahead of the swap in each step (see stream_insert).
+#ifndef BURR_BAND_LOOKAHEAD
+#define BURR_BAND_LOOKAHEAD 3
+#endif
+constexpr int kLook = BURR_BAND_LOOKAHEAD;
+static_assert(kLook >= 0 && kLook <= 8, "lookahead out of range");
+
 // Stream staged rows [lo, hi) (index range) into the band; stored ring
 // indices are appended to S.clist (from S.ncommit).  Returns kOk, kDependent
 // or kOverflow; nothing is rolled back here.  Every lane takes one step per
 // iteration; stores, the commit list and the hand-out of the next rows go by
 // ballot and prefix count, with no shared atomics besides the swaps.
+//
+// Lookahead: beside the swap on the slot of its leading bit p, a lane reads
+// the slots p+1 .. p+kLook with plain loads (in flight together with the
+// swap).  When the swap returns a stored row, elimination goes on through
+// those slots without another round trip: a slot read as occupied holds a
+// final equation, so XORing it is the step the swap would have taken; the
+// step ends at the first leading bit whose slot was not read as occupied,
+// and the next swap goes there.  The row is kept as 64 bits from p plus the
+// kLook bits beyond p+63 that the read-ahead rows bring in.
 __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
@@ -202,18 +236,48 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
     int result = kOk;
     while (__any_sync(kFull, has)) {
         unsigned long long oc = 0, oy = 0;
-        if (has) slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
+        unsigned long long lc[kLook > 0 ? kLook : 1], ly[kLook > 0 ? kLook : 1];
+        if (has) {
+#pragma unroll
+            for (int j = 0; j < kLook; ++j) slot_load(&S.ring[(pos + 1u + (uint32_t)j) & kRingMask], lc[j], ly[j]);
+            slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
+        }
         const bool stored = has && oc == 0ull;
         bool dep = false, ovf = false;
         if (has && !stored) {
             cur ^= oc;
-            y ^= oy & ~kYValid;
-            dep = cur == 0ull;
-            const uint32_t lo32 = (uint32_t)cur;
-            const int tz = dep ? 0 : (lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(cur >> 32)));
-            cur >>= tz;
-            pos += (uint32_t)tz;
-            ovf = !dep && pos - bB >= (uint32_t)kRing;
+            y ^= (uint32_t)oy;   // right-hand sides fit in 32 bits; bit 32 (kYValid) stays set
+            // cur: bit j = slot pos + j, bit 0 now clear; over: bit j = slot pos + 64 + j
+            uint32_t over = 0;
+            // a read-ahead slot past the live window would alias an older slot: none is used near its end
+            bool go = pos - bB + (uint32_t)kLook < (uint32_t)kRing;
+#pragma unroll
+            for (int j = 1; j <= kLook; ++j) {
+                // while go holds, bits 0 .. j-1 of cur are clear, so bit j is the leading bit if set;
+                // a stored row has its pivot bit (bit 0) set and its right-hand side marked valid
+                const bool bit = ((uint32_t)cur >> j) & 1u;
+                const bool occ = ((uint32_t)lc[j - 1] & (uint32_t)(ly[j - 1] >> 32) & 1u) != 0u;
+                if (go && bit && occ) {
+                    cur ^= lc[j - 1] << j;
+                    over ^= (uint32_t)(lc[j - 1] >> (64 - j));
+                    y ^= (uint32_t)ly[j - 1];
+                }
+                go = go && (!bit || occ);
+            }
+            dep = cur == 0ull && over == 0u;
+            if (!dep) {
+                int tz;
+                if (cur != 0ull) {
+                    tz = ctz64(cur);   // >= 1
+                    cur = (cur >> tz) | (kLook > 0 ? (unsigned long long)over << (64 - tz) : 0ull);
+                } else {
+                    const int t2 = __ffs((int)over) - 1;
+                    tz = 64 + t2;
+                    cur = (unsigned long long)(over >> t2);
+                }
+                pos += (uint32_t)tz;
+                ovf = pos - bB >= (uint32_t)kRing;
+            }
         }
         const unsigned sm = __ballot_sync(kFull, stored);
         const uint32_t rank = (uint32_t)__popc(sm & lt);
