@@ -60,12 +60,24 @@ struct alignas(16) RingSlot {
     unsigned long long y;   // kYValid | right-hand side (low r bits); 0 = empty
 };
 
+// A staged equation: one 16-byte read hands it to a lane.
+struct alignas(16) StagedRow {
+    unsigned long long c;   // coefficient row (bit 0 = start slot)
+    uint32_t y;             // right-hand side
+    uint32_t o;             // offset of the start slot in its bucket
+};
+
+// Ring slots read ahead of the swap in each step (see stream_insert).
+#ifndef BURR_BAND_LOOKAHEAD
+#define BURR_BAND_LOOKAHEAD 3
+#endif
+constexpr int kLook = BURR_BAND_LOOKAHEAD;
+static_assert(kLook >= 0 && kLook <= 8, "lookahead out of range");
+
 struct BandWarpSmem {
-    RingSlot ring[kRing];          // live band window
+    RingSlot ring[kRing + kLook];  // live band window (+ read-ahead pad, never written)
     uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
-    unsigned long long rc[kStage]; // staged coefficient rows, ascending offset
-    uint32_t ry[kStage];           // staged right-hand sides
-    uint8_t ro[kStage];            // staged offsets
+    StagedRow rows[kStage];        // staged equations, ascending offset
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
     uint32_t ncommit;              // entries of clist
 };
@@ -159,9 +171,7 @@ __device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, 
         const uint32_t i = (uint32_t)lane + 32u * j;
         if (i < cnt) {
             const uint32_t p = S.first[o[j]] + rank[j];
-            S.rc[p] = c[j];
-            S.ry[p] = y[j];
-            S.ro[p] = (uint8_t)o[j];
+            S.rows[p] = StagedRow{c[j], y[j], o[j]};
         }
     }
     __syncwarp();
@@ -169,9 +179,8 @@ __device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, 
 
 // 128-bit compare-and-swap on a ring slot: if the slot is (0, 0) it becomes
 // (c, y); the previous contents are returned either way.
-__device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, unsigned long long y,
+__device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, unsigned long long y,
                                          unsigned long long &oc, unsigned long long &oy) {
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
     const unsigned long long zero = 0ull;
     asm volatile("{\n\t.reg .b128 d, b, v;\n\t"
                  "mov.b128 b, {%2, %2};\n\t"
@@ -188,23 +197,9 @@ __device__ __forceinline__ void slot_cas(RingSlot *slot, unsigned long long c, u
 // and a valid right-hand side has seen a stored equation that stays; any
 // other result (empty, or a torn read of a slot being written) is treated as
 // "not known to be occupied".
-__device__ __forceinline__ void slot_load(const RingSlot *slot, unsigned long long &c, unsigned long long &y) {
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
+__device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, unsigned long long &y) {
     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c), "=l"(y) : "r"(addr) : "memory");
 }
-
-// Index of the lowest set bit of a nonzero 64-bit word.
-__device__ __forceinline__ int ctz64(unsigned long long v) {
-    const uint32_t lo32 = (uint32_t)v;
-    return lo32 ? __ffs((int)lo32) - 1 : 31 + __ffs((int)(uint32_t)(v >> 32));
-}
-
-// Ring slots read ahead of the swap in each step (see stream_insert).
-#ifndef BURR_BAND_LOOKAHEAD
-#define BURR_BAND_LOOKAHEAD 3
-#endif
-constexpr int kLook = BURR_BAND_LOOKAHEAD;
-static_assert(kLook >= 0 && kLook <= 8, "lookahead out of range");
 
 // Stream staged rows [lo, hi) (index range) into the band; stored ring
 // indices are appended to S.clist (from S.ncommit).  Returns kOk, kDependent
@@ -223,79 +218,84 @@ static_assert(kLook >= 0 && kLook <= 8, "lookahead out of range");
 __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
+    const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&S.ring[0]);
     uint32_t next = lo + 32u, nc = S.ncommit;
-    uint32_t idx = lo + (uint32_t)lane;
-    bool has = idx < hi;
+    bool has = lo + (uint32_t)lane < hi;
+    // a lane without a row swaps (0, 0) in, which leaves every slot as it was
     unsigned long long cur = 0, y = 0;
-    uint32_t pos = 0;
+    uint32_t pos = bB;
     if (has) {
-        cur = S.rc[idx];
-        y = kYValid | S.ry[idx];
-        pos = bB + S.ro[idx];
+        const StagedRow r = S.rows[lo + (uint32_t)lane];
+        cur = r.c;
+        y = kYValid | r.y;
+        pos = bB + r.o;
     }
     int result = kOk;
-    while (__any_sync(kFull, has)) {
-        unsigned long long oc = 0, oy = 0;
+    unsigned flags = __reduce_or_sync(kFull, has ? 1u : 0u);
+    while (flags & 1u) {
+        const uint32_t ri = pos & kRingMask;
+        const unsigned addr = ring0 + ri * (unsigned)sizeof(RingSlot);
+        unsigned long long oc, oy;
         unsigned long long lc[kLook > 0 ? kLook : 1], ly[kLook > 0 ? kLook : 1];
-        if (has) {
 #pragma unroll
-            for (int j = 0; j < kLook; ++j) slot_load(&S.ring[(pos + 1u + (uint32_t)j) & kRingMask], lc[j], ly[j]);
-            slot_cas(&S.ring[pos & kRingMask], cur, y, oc, oy);
-        }
+        for (int j = 0; j < kLook; ++j) slot_load(addr + (unsigned)((j + 1) * sizeof(RingSlot)), lc[j], ly[j]);
+        slot_cas(addr, cur, y, oc, oy);
         const bool stored = has && oc == 0ull;
-        bool dep = false, ovf = false;
-        if (has && !stored) {
-            cur ^= oc;
-            y ^= (uint32_t)oy;   // right-hand sides fit in 32 bits; bit 32 (kYValid) stays set
-            // cur: bit j = slot pos + j, bit 0 now clear; over: bit j = slot pos + 64 + j
-            uint32_t over = 0;
-            // a read-ahead slot past the live window would alias an older slot: none is used near its end
-            bool go = pos - bB + (uint32_t)kLook < (uint32_t)kRing;
+        const bool act = has && !stored;
+        // eliminate against the swapped slot, then through the read-ahead slots
+        unsigned long long c2 = cur ^ oc;
+        unsigned long long y2 = y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits; kYValid stays set
+        // c2: bit j = slot pos + j, bit 0 now clear; over: bit j = slot pos + 64 + j.  A read-ahead
+        // slot past the live window would alias an older slot, and one past the ring's end is the
+        // pad: neither is used.
+        uint32_t over = 0;
+        bool go = pos - bB + (uint32_t)kLook < (uint32_t)kRing && ri + (uint32_t)kLook < (uint32_t)kRing;
 #pragma unroll
-            for (int j = 1; j <= kLook; ++j) {
-                // while go holds, bits 0 .. j-1 of cur are clear, so bit j is the leading bit if set;
-                // a stored row has its pivot bit (bit 0) set and its right-hand side marked valid
-                const bool bit = ((uint32_t)cur >> j) & 1u;
-                const bool occ = ((uint32_t)lc[j - 1] & (uint32_t)(ly[j - 1] >> 32) & 1u) != 0u;
-                if (go && bit && occ) {
-                    cur ^= lc[j - 1] << j;
-                    over ^= (uint32_t)(lc[j - 1] >> (64 - j));
-                    y ^= (uint32_t)ly[j - 1];
-                }
-                go = go && (!bit || occ);
-            }
-            dep = cur == 0ull && over == 0u;
-            if (!dep) {
-                int tz;
-                if (cur != 0ull) {
-                    tz = ctz64(cur);   // >= 1
-                    cur = (cur >> tz) | (kLook > 0 ? (unsigned long long)over << (64 - tz) : 0ull);
-                } else {
-                    const int t2 = __ffs((int)over) - 1;
-                    tz = 64 + t2;
-                    cur = (unsigned long long)(over >> t2);
-                }
-                pos += (uint32_t)tz;
-                ovf = pos - bB >= (uint32_t)kRing;
-            }
+        for (int j = 1; j <= kLook; ++j) {
+            // while go holds, bits 0 .. j-1 of c2 are clear, so bit j is the leading bit if set;
+            // a stored row has its pivot bit (bit 0) set and its right-hand side marked valid
+            const bool bit = ((uint32_t)c2 >> j) & 1u;
+            const bool occ = ((uint32_t)lc[j - 1] & (uint32_t)(ly[j - 1] >> 32) & 1u) != 0u;
+            const bool use = go && bit && occ;
+            c2 ^= use ? lc[j - 1] << j : 0ull;
+            over ^= use ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
+            y2 ^= use ? (uint32_t)ly[j - 1] : 0u;
+            go = go && (!bit || occ);
+        }
+        const uint32_t lo32 = (uint32_t)c2, hi32 = (uint32_t)(c2 >> 32);
+        const bool zero = (lo32 | hi32 | over) == 0u;
+        // leading bit of (over : c2); >= 1 for an active lane, whose bit 0 was just cleared
+        const int tz = lo32 ? __ffs((int)lo32) - 1 : hi32 ? 31 + __ffs((int)hi32) : 63 + __ffs((int)over);
+        const unsigned long long ncur = tz < 64 ? (c2 >> (tz & 63)) | ((unsigned long long)over << ((64 - tz) & 63))
+                                                : (unsigned long long)(over >> ((tz - 64) & 31));
+        const uint32_t npos = pos + (uint32_t)tz;
+        const bool dep = act && zero;
+        const bool ovf = act && !zero && npos - bB >= (uint32_t)kRing;
+        if (act) {
+            cur = ncur;
+            y = y2;
+            pos = npos;
         }
         const unsigned sm = __ballot_sync(kFull, stored);
         const uint32_t rank = (uint32_t)__popc(sm & lt);
         if (stored) {
-            S.clist[nc + rank] = (uint16_t)(pos & kRingMask);
-            idx = next + rank;
+            S.clist[nc + rank] = (uint16_t)ri;
+            const uint32_t idx = next + rank;
             has = idx < hi;
+            cur = 0;
+            y = 0;
             if (has) {
-                cur = S.rc[idx];
-                y = kYValid | S.ry[idx];
-                pos = bB + S.ro[idx];
+                const StagedRow r = S.rows[idx];
+                cur = r.c;
+                y = kYValid | r.y;
+                pos = bB + r.o;
             }
         }
         nc += (uint32_t)__popc(sm);
         next += (uint32_t)__popc(sm);
-        const unsigned bad = __ballot_sync(kFull, dep || ovf);
-        if (bad) {
-            result = __ballot_sync(kFull, ovf) ? kOverflow : kDependent;
+        flags = __reduce_or_sync(kFull, (has ? 1u : 0u) | (dep ? 2u : 0u) | (ovf ? 4u : 0u));
+        if (flags & 6u) {
+            result = (flags & 4u) ? kOverflow : kDependent;
             break;
         }
     }
