@@ -192,6 +192,10 @@ __device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, un
                  : "memory");
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.L2 [%0];" ::"l"(p));
+}
+
 // Plain 128-bit read of a ring slot.  A slot goes from empty to its final
 // contents once per set (one atomic write), so a read that sees a nonzero row
 // and a valid right-hand side has seen a stored equation that stays; any
@@ -444,8 +448,23 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
 
     uint64_t flushed = own_lo;
     uint64_t tword = 0, twi = b0 >> 5;
+    // bucket bounds are read one bucket ahead, and the next bucket's equations are
+    // prefetched into L2, so that staging does not wait on DRAM
+    const uint32_t *bst = a.bstart + x.bucket_base;
+    const uint32_t pend = bst[b1];   // end of the partition's equations
+    uint32_t nrs = b0 < b1 ? bst[b0] : 0, nre = b0 < b1 ? bst[b0 + 1] : 0;
     for (uint64_t b = b0; b < b1; ++b) {
         const uint64_t bB = b * L.B;
+        const uint32_t rs = nrs, re = nre;
+        nrs = re;
+        nre = b + 2 <= b1 ? bst[b + 2] : re;
+        if (lane < 16) {
+            const uint32_t k = re + (uint32_t)lane * (128u / sizeof(uint64_t));
+            if (k < pend) prefetch_l2(a.keys + k);
+        } else if (lane < 24) {
+            const uint32_t k = re + (uint32_t)(lane - 16) * (128u / sizeof(V));
+            if (k < pend) prefetch_l2(a.vals + k);
+        }
         if (bB > flushed) {
             flush(S, a, x, flushed, bB, lane);
             flushed = bB;
@@ -454,7 +473,6 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         const uint32_t forced = cut ? (kExact ? (uint32_t)kW : flevel) : 0;
         uint32_t code = cut ? fcode : 0;
         uint32_t texact = forced;
-        const uint32_t rs = a.bstart[x.bucket_base + b], re = a.bstart[x.bucket_base + b + 1];
         if (re > rs) {
             uint32_t staged = 0xffffffffu;
             int rc = insert_set(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
@@ -471,14 +489,19 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                     code = 3;
                     for (int k = 2; k >= 0; --k) {
                         if (lv[k + 1] <= forced) break;
-                        const uint32_t lo = max(lv[k], forced), hi = lv[k + 1];
-                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lo, hi, staged, lane);
+                        // with every band above it kept, the band that reaches down to `forced`
+                        // completes the set [forced, B), which was just found dependent
+                        if (lv[k] <= forced) {
+                            code = (uint32_t)k + 1;
+                            break;
+                        }
+                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lv[k], lv[k + 1], staged, lane);
                         if (rc2 == kOverflow) return;
                         if (rc2 == kDependent) {
                             code = (uint32_t)k + 1;
                             break;
                         }
-                        code = (lv[k] >= forced) ? (uint32_t)k : fcode;
+                        code = (uint32_t)k;
                     }
                 }
             }
