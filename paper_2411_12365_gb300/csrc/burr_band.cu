@@ -235,73 +235,96 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         pos = bB + r.o;
     }
     int result = kOk;
-    unsigned flags = __reduce_or_sync(kFull, has ? 1u : 0u);
-    while (flags & 1u) {
+    for (;;) {
         const uint32_t ri = pos & kRingMask;
         const unsigned addr = ring0 + ri * (unsigned)sizeof(RingSlot);
+        // A read-ahead slot past the live window would alias an older slot, and one past the
+        // ring's end is the pad: near either, no read-ahead slot is used.
+        const bool win = pos - bB + (uint32_t)kLook < (uint32_t)kRing && ri + (uint32_t)kLook < (uint32_t)kRing;
         unsigned long long oc, oy;
         unsigned long long lc[kLook > 0 ? kLook : 1], ly[kLook > 0 ? kLook : 1];
 #pragma unroll
         for (int j = 0; j < kLook; ++j) slot_load(addr + (unsigned)((j + 1) * sizeof(RingSlot)), lc[j], ly[j]);
         slot_cas(addr, cur, y, oc, oy);
         const bool stored = has && oc == 0ull;
+
+        // Hand-out first: the next row's shared read is in flight during the elimination.
+        const unsigned sm = __ballot_sync(kFull, stored);
+        const uint32_t rank = (uint32_t)__popc(sm & lt);
+        const uint32_t nidx = next + rank;
+        const bool nhas = stored && nidx < hi;
+        StagedRow nr = StagedRow{0ull, 0u, 0u};
+        if (nhas) nr = S.rows[nidx];
+        if (stored) S.clist[nc + rank] = (uint16_t)ri;
+        nc += (uint32_t)__popc(sm);
+        next += (uint32_t)__popc(sm);
+
+        // Elimination for lanes whose swap returned a stored row: against that row, then through
+        // the read-ahead slots.  The row is (over : hi32 : lo32), bit j = slot pos + j; bit 0 is
+        // now clear.  Which read-ahead rows are used depends only on the low word, so the
+        // decisions run on 32 bits and the other words are XORed afterwards, all at once.
         const bool act = has && !stored;
-        // eliminate against the swapped slot, then through the read-ahead slots
-        unsigned long long c2 = cur ^ oc;
-        unsigned long long y2 = y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits; kYValid stays set
-        // c2: bit j = slot pos + j, bit 0 now clear; over: bit j = slot pos + 64 + j.  A read-ahead
-        // slot past the live window would alias an older slot, and one past the ring's end is the
-        // pad: neither is used.
+        uint32_t lo32 = (uint32_t)cur ^ (uint32_t)oc;
+        uint32_t hi32 = (uint32_t)(cur >> 32) ^ (uint32_t)(oc >> 32);
         uint32_t over = 0;
-        bool go = pos - bB + (uint32_t)kLook < (uint32_t)kRing && ri + (uint32_t)kLook < (uint32_t)kRing;
+        uint32_t y2 = (uint32_t)y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits
+        bool go = win;
+        bool use[kLook > 0 ? kLook : 1];
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
-            // while go holds, bits 0 .. j-1 of c2 are clear, so bit j is the leading bit if set;
-            // a stored row has its pivot bit (bit 0) set and its right-hand side marked valid
-            const bool bit = ((uint32_t)c2 >> j) & 1u;
+            // while go holds, bits 0 .. j-1 are clear, so bit j is the leading bit if set; a stored
+            // row has its pivot bit (bit 0) set and its right-hand side marked valid
             const bool occ = ((uint32_t)lc[j - 1] & (uint32_t)(ly[j - 1] >> 32) & 1u) != 0u;
-            const bool use = go && bit && occ;
-            c2 ^= use ? lc[j - 1] << j : 0ull;
-            over ^= use ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
-            y2 ^= use ? (uint32_t)ly[j - 1] : 0u;
+            const bool bit = (lo32 >> j) & 1u;
+            use[j - 1] = go && bit && occ;
+            lo32 ^= use[j - 1] ? (uint32_t)lc[j - 1] << j : 0u;
             go = go && (!bit || occ);
         }
-        const uint32_t lo32 = (uint32_t)c2, hi32 = (uint32_t)(c2 >> 32);
+#pragma unroll
+        for (int j = 1; j <= kLook; ++j) {
+            const unsigned long long sh = lc[j - 1] << j;
+            hi32 ^= use[j - 1] ? (uint32_t)(sh >> 32) : 0u;
+            over ^= use[j - 1] ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
+            y2 ^= use[j - 1] ? (uint32_t)ly[j - 1] : 0u;
+        }
+        // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0
         const bool zero = (lo32 | hi32 | over) == 0u;
-        // leading bit of (over : c2); >= 1 for an active lane, whose bit 0 was just cleared
         const int tz = lo32 ? __ffs((int)lo32) - 1 : hi32 ? 31 + __ffs((int)hi32) : 63 + __ffs((int)over);
-        const unsigned long long ncur = tz < 64 ? (c2 >> (tz & 63)) | ((unsigned long long)over << ((64 - tz) & 63))
-                                                : (unsigned long long)(over >> ((tz - 64) & 31));
+        uint32_t w0 = lo32, w1 = hi32, w2 = over;
+        int t = tz;
+        if (t >= 32) {
+            w0 = w1;
+            w1 = w2;
+            w2 = 0;
+            t -= 32;
+        }
+        if (t >= 32) {
+            w0 = w1;
+            w1 = 0;
+            t -= 32;
+        }
+        const uint32_t n0 = __funnelshift_r(w0, w1, (unsigned)t), n1 = __funnelshift_r(w1, w2, (unsigned)t);
         const uint32_t npos = pos + (uint32_t)tz;
         const bool dep = act && zero;
         const bool ovf = act && !zero && npos - bB >= (uint32_t)kRing;
         if (act) {
-            cur = ncur;
-            y = y2;
+            cur = ((unsigned long long)n1 << 32) | n0;
+            y = kYValid | y2;
             pos = npos;
         }
-        const unsigned sm = __ballot_sync(kFull, stored);
-        const uint32_t rank = (uint32_t)__popc(sm & lt);
         if (stored) {
-            S.clist[nc + rank] = (uint16_t)ri;
-            const uint32_t idx = next + rank;
-            has = idx < hi;
-            cur = 0;
-            y = 0;
-            if (has) {
-                const StagedRow r = S.rows[idx];
-                cur = r.c;
-                y = kYValid | r.y;
-                pos = bB + r.o;
-            }
+            has = nhas;
+            cur = nr.c;
+            y = nhas ? kYValid | nr.y : 0ull;
+            if (nhas) pos = bB + nr.o;
         }
-        nc += (uint32_t)__popc(sm);
-        next += (uint32_t)__popc(sm);
-        flags = __reduce_or_sync(kFull, (has ? 1u : 0u) | (dep ? 2u : 0u) | (ovf ? 4u : 0u));
-        if (flags & 6u) {
-            result = (flags & 4u) ? kOverflow : kDependent;
+        const unsigned bm = __ballot_sync(kFull, dep || ovf);
+        const unsigned hm = __ballot_sync(kFull, has);
+        if (bm) {
+            result = __ballot_sync(kFull, ovf) ? kOverflow : kDependent;
             break;
         }
+        if (!hm) break;
     }
     __syncwarp();
     if (lane == 0) S.ncommit = nc;
