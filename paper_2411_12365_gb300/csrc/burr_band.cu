@@ -26,8 +26,9 @@
 //     on the ring slot of the row's leading bit, which either claims the
 //     slot if it is empty (row and right-hand side stored in one atomic
 //     write) or returns the stored row and right-hand side to XOR with.  Plain
-//     reads of the next three slots are in flight beside the swap, and the
-//     elimination goes on through those that hold stored rows.  This
+//     reads of the next few slots (two with 2-bit thresholds, three with
+//     1+-bit ones) are in flight beside the swap, and the elimination goes on
+//     through those that hold stored rows.  This
 //     is a sequential insertion in claim order: every slot a row eliminated
 //     against was occupied when read and stays so, and a row is stored only
 //     on a slot that was still empty.  Lanes whose row was stored take the
@@ -67,15 +68,27 @@ struct alignas(16) StagedRow {
     uint32_t o;             // offset of the start slot in its bucket
 };
 
-// Ring slots read ahead of the swap in each step (see stream_insert).
-#ifndef BURR_BAND_LOOKAHEAD
-#define BURR_BAND_LOOKAHEAD 3
+// Ring slots read ahead of the swap in each step (see stream_insert), per
+// threshold mode: more read-ahead means fewer steps but more instructions per
+// step.  Buckets with 2-bit thresholds are inserted as large sets, where many
+// warps per SM compete for issue slots; the 1+-bit search inserts many small
+// sets, whose time is their number of steps.
+#ifndef BURR_BAND_LOOKAHEAD_2BIT
+#define BURR_BAND_LOOKAHEAD_2BIT 2
 #endif
-constexpr int kLook = BURR_BAND_LOOKAHEAD;
-static_assert(kLook >= 0 && kLook <= 8, "lookahead out of range");
+#ifndef BURR_BAND_LOOKAHEAD_1PLUS
+#define BURR_BAND_LOOKAHEAD_1PLUS 3
+#endif
+template <bool kExact>
+struct Lookahead {
+    static constexpr int value = kExact ? BURR_BAND_LOOKAHEAD_1PLUS : BURR_BAND_LOOKAHEAD_2BIT;
+    static_assert(value >= 0 && value <= 8, "lookahead out of range");
+};
+constexpr int kLookMax = Lookahead<false>::value > Lookahead<true>::value ? Lookahead<false>::value
+                                                                          : Lookahead<true>::value;
 
 struct BandWarpSmem {
-    RingSlot ring[kRing + kLook];  // live band window (+ read-ahead pad, never written)
+    RingSlot ring[kRing + kLookMax];   // live band window (+ read-ahead pad, never written)
     uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
     StagedRow rows[kStage];        // staged equations, ascending offset
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
@@ -219,6 +232,7 @@ __device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, 
 // step ends at the first leading bit whose slot was not read as occupied,
 // and the next swap goes there.  The row is kept as 64 bits from p plus the
 // kLook bits beyond p+63 that the read-ahead rows bring in.
+template <int kLook>
 __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
@@ -246,7 +260,8 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 #pragma unroll
         for (int j = 0; j < kLook; ++j) slot_load(addr + (unsigned)((j + 1) * sizeof(RingSlot)), lc[j], ly[j]);
         slot_cas(addr, cur, y, oc, oy);
-        const bool stored = has && oc == 0ull;
+        // an empty slot is all zero and a stored row has its pivot bit set
+        const bool stored = has && ((uint32_t)oc & 1u) == 0u;
 
         // Hand-out first: the next row's shared read is in flight during the elimination.
         const unsigned sm = __ballot_sync(kFull, stored);
@@ -287,23 +302,23 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
             over ^= use[j - 1] ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
             y2 ^= use[j - 1] ? (uint32_t)ly[j - 1] : 0u;
         }
-        // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0
-        const bool zero = (lo32 | hi32 | over) == 0u;
-        const int tz = lo32 ? __ffs((int)lo32) - 1 : hi32 ? 31 + __ffs((int)hi32) : 63 + __ffs((int)over);
-        uint32_t w0 = lo32, w1 = hi32, w2 = over;
-        int t = tz;
-        if (t >= 32) {
-            w0 = w1;
-            w1 = w2;
-            w2 = 0;
-            t -= 32;
+        // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0; it is
+        // almost always in the low word
+        int tz = __ffs((int)lo32) - 1;
+        uint32_t n0 = __funnelshift_r(lo32, hi32, (unsigned)tz), n1 = __funnelshift_r(hi32, over, (unsigned)tz);
+        bool zero = false;
+        if (act && lo32 == 0u) {
+            zero = (hi32 | over) == 0u;
+            if (hi32) {
+                tz = 31 + __ffs((int)hi32);
+                n0 = __funnelshift_r(hi32, over, (unsigned)(tz - 32));
+                n1 = over >> (tz - 32);
+            } else {
+                tz = 63 + __ffs((int)over);
+                n0 = over >> ((tz - 64) & 31);
+                n1 = 0;
+            }
         }
-        if (t >= 32) {
-            w0 = w1;
-            w1 = 0;
-            t -= 32;
-        }
-        const uint32_t n0 = __funnelshift_r(w0, w1, (unsigned)t), n1 = __funnelshift_r(w1, w2, (unsigned)t);
         const uint32_t npos = pos + (uint32_t)tz;
         const bool dep = act && zero;
         const bool ovf = act && !zero && npos - bB >= (uint32_t)kRing;
@@ -334,7 +349,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 
 // Insert the rows of bucket [rs, re) whose offset lies in [olo, ohi) as one
 // set; on a dependency or overflow every row this call stored is removed.
-template <typename V>
+template <typename V, bool kExact>
 __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
                           uint32_t bB, uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
     if (lane == 0) S.ncommit = 0;
@@ -345,7 +360,7 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
             stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
-        const int rc = stream_insert(S, S.first[olo], S.first[ohi], bB, lane);
+        const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, lane);
         if (rc != kOk) {
             rollback(S, S.ncommit, lane);
             if (rc == kOverflow && lane == 0) atomicOr(a.err, kErrRingOverflow);
@@ -370,7 +385,7 @@ __device__ __forceinline__ uint32_t exact_threshold(BandWarpSmem &S, const BandA
     while (t_ok - t_fail > 1) {
         const uint32_t mid = (first && t_fail + 16u < t_ok) ? t_fail + 16u : (t_fail + t_ok) >> 1;
         first = false;
-        const int rc = insert_set(S, a, x, rs, re, bB, mid, t_ok, staged, lane);
+        const int rc = insert_set<V, true>(S, a, x, rs, re, bB, mid, t_ok, staged, lane);
         if (rc == kOverflow) return x.L.B + 1u;
         if (rc == kOk) t_ok = mid;
         else t_fail = mid;
@@ -498,7 +513,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         uint32_t texact = forced;
         if (re > rs) {
             uint32_t staged = 0xffffffffu;
-            int rc = insert_set(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
+            int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
             if (rc == kOverflow) return;
             if (rc == kDependent) {
                 if (L.fallback) {
@@ -518,7 +533,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                             code = (uint32_t)k + 1;
                             break;
                         }
-                        const int rc2 = insert_set(S, a, x, rs, re, (uint32_t)bB, lv[k], lv[k + 1], staged, lane);
+                        const int rc2 = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, lv[k], lv[k + 1], staged,
+                                                              lane);
                         if (rc2 == kOverflow) return;
                         if (rc2 == kDependent) {
                             code = (uint32_t)k + 1;
