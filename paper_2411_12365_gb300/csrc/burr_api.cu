@@ -669,6 +669,7 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
         T.slots += m;
         T.tw += (D.L.nb + 31) / 32;
         T.zw += (m / 64) * r[s];
+        T.zw = (T.zw + 3) & ~3ull;   // every structure's table starts on 32 bytes (wide query loads)
         T.nkeys += n[s];
     }
     return BURR_OK;

@@ -32,19 +32,42 @@ __device__ __forceinline__ uint32_t eval_window(const uint64_t *__restrict__ z, 
 
 // The 2r table words around slot s (blocks s/64 and s/64 + 1), loaded before
 // the threshold is known so that both reads are in flight together; R is the
-// value width fixed at compile time.
+// value width fixed at compile time.  The second block is needed only when the
+// window is not block-aligned, and a window that starts at the last block
+// (s = m - 64) has no second block inside the table: it is not read then.
 template <int R>
 struct Window {
     uint64_t w0[R], w1[R];
 };
 
-template <int R>
+// 32-byte read-only global load (four table words).
+__device__ __forceinline__ void ldg_v4(const uint64_t *p, uint64_t &a, uint64_t &b, uint64_t &c, uint64_t &d) {
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+
+// kWide: the table starts on 32 bytes and R is a multiple of 4, so each block
+// of R words is read in R/4 32-byte loads (checked by the launcher).  Narrow
+// reads of random windows cost one L1 wavefront per word and warp lane.
+template <int R, bool kWide>
 __device__ __forceinline__ void load_window(const uint64_t *__restrict__ z, uint32_t s, Window<R> &w) {
     const uint64_t *p = z + (uint64_t)(s >> 6) * R;
+    const bool two = (s & 63u) != 0u;
+    if constexpr (kWide) {
+        static_assert(R % 4 == 0, "wide window loads need R % 4 == 0");
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        w.w0[k] = __ldg(p + k);
-        w.w1[k] = __ldg(p + R + k);
+        for (int k = 0; k < R; k += 4) ldg_v4(p + k, w.w0[k], w.w0[k + 1], w.w0[k + 2], w.w0[k + 3]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) w.w1[k] = 0;
+        if (two) {
+#pragma unroll
+            for (int k = 0; k < R; k += 4) ldg_v4(p + R + k, w.w1[k], w.w1[k + 1], w.w1[k + 2], w.w1[k + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            w.w0[k] = __ldg(p + k);
+            w.w1[k] = two ? __ldg(p + R + k) : 0ull;
+        }
     }
 }
 
@@ -77,7 +100,7 @@ __device__ __forceinline__ uint32_t threshold_of(const QueryDesc &Q, uint32_t l,
 
 // Query kernel for a value width R known at compile time: the table window
 // of a layer is loaded together with its threshold.
-template <typename V, int R>
+template <typename V, int R, bool kWide>
 __global__ void __launch_bounds__(kQThreads)
 k_query_r(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, uint64_t n) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -92,7 +115,7 @@ k_query_r(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, u
             const uint64_t h = mix64(key ^ Q.sigma[l]);
             const uint32_t s = (uint32_t)__umul64hi(h, m - kW + 1);
             Window<R> w;
-            load_window<R>(Q.z[l], s, w);
+            load_window<R, kWide>(Q.z[l], s, w);
             if ((s & (Q.B - 1)) < threshold_of(Q, l, s >> log2B)) continue;   // bumped: next layer
             v = eval_loaded<R>(w, s, mix64(h + Q.sigma[l]) | 1ull);
             break;
@@ -101,7 +124,7 @@ k_query_r(QueryDesc Q, const uint64_t *__restrict__ keys, V *__restrict__ out, u
             const uint64_t h = mix64(key ^ Q.sigma[l]);
             const uint32_t s = (uint32_t)__umul64hi(h, Q.m[l] - kW + 1);
             Window<R> w;
-            load_window<R>(Q.z[l], s, w);
+            load_window<R, kWide>(Q.z[l], s, w);
             v = eval_loaded<R>(w, s, mix64(h + Q.sigma[l]) | 1ull);
         }
         out[i] = (V)v;
@@ -156,17 +179,23 @@ cudaError_t launch_query(const QueryDesc &Q, uint32_t vbytes, const uint64_t *ke
                          cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const unsigned grid = grid_for(n, kQThreads, 152u * 64u);
-    // common widths: the window is loaded together with the threshold
+    // common widths: the window is loaded together with the threshold, in 32-byte reads when
+    // every table of the structure starts on 32 bytes
+    bool wide = true;
+    for (uint32_t l = 0; l <= Q.layers; ++l)
+        if (Q.m[l] != 0 && ((uintptr_t)Q.z[l] & 31u) != 0) wide = false;
     if (Q.r == 8 && vbytes == 1) {
-        k_query_r<uint8_t, 8><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
+        if (wide) k_query_r<uint8_t, 8, true><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
+        else k_query_r<uint8_t, 8, false><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
         return cudaGetLastError();
     }
     if (Q.r == 1 && vbytes == 1) {
-        k_query_r<uint8_t, 1><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
+        k_query_r<uint8_t, 1, false><<<grid, kQThreads, 0, st>>>(Q, keys, (uint8_t *)out, n);
         return cudaGetLastError();
     }
     if (Q.r == 16 && vbytes == 2) {
-        k_query_r<uint16_t, 16><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n);
+        if (wide) k_query_r<uint16_t, 16, true><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n);
+        else k_query_r<uint16_t, 16, false><<<grid, kQThreads, 0, st>>>(Q, keys, (uint16_t *)out, n);
         return cudaGetLastError();
     }
     switch (vbytes) {
