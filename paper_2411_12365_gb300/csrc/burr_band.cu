@@ -656,6 +656,112 @@ k_backsub(LayerDesc L0, const uint64_t *__restrict__ Cg0, const V *__restrict__ 
     }
 }
 
+// Back-substitution of a single structure's layer with several partitions per
+// warp: a partition needs only r lanes (one per bit plane), so the warp solves
+// G = min(32 / r, kBsGroups) partitions side by side, lanes [q*r, q*r + r) on
+// partition q.  The arithmetic is that of k_backsub; sharing each instruction
+// among G partitions cuts the issue load G-fold, which matters because the
+// solve runs beside the next layer's sort and band.  Partitions of one warp may
+// differ in length: each walks its own blocks from the right, and a finished
+// group idles until the longest one is done.
+constexpr int kBsGroups = 8;
+
+template <typename V>
+__global__ void __launch_bounds__(32 * kBsWarps)
+k_backsub_multi(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z,
+                uint32_t G) {
+    __shared__ uint64_t sc[kBsWarps][kBsGroups][64];
+    __shared__ uint32_t sy[kBsWarps][kBsGroups][64];
+    __shared__ uint64_t shi[kBsWarps][kBsGroups];   // one past the last block of each group's partition
+    __shared__ uint32_t slen[kBsWarps][kBsGroups];  // its number of blocks
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t R = L.r;
+    const uint32_t q = (uint32_t)lane / R, k = (uint32_t)lane % R;
+    const uint64_t part0 = ((uint64_t)blockIdx.x * kBsWarps + warp) * G;
+    uint64_t bhi = 0;
+    uint32_t len = 0;
+    if (q < G && part0 + q < L.K) {
+        const uint64_t lo = part_own_lo(L, part0 + q) >> 6, hi = part_own_hi(L, part0 + q) >> 6;
+        if (hi > lo) {
+            bhi = hi;
+            len = (uint32_t)(hi - lo);
+        }
+    }
+    if (q < G && k == 0) {
+        shi[warp][q] = bhi;
+        slen[warp][q] = len;
+    }
+    const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+    __syncwarp();
+    if (maxlen == 0) return;
+    uint64_t gh[kBsGroups];
+    uint32_t gl[kBsGroups];
+#pragma unroll
+    for (int g = 0; g < kBsGroups; ++g) {
+        gh[g] = (uint32_t)g < G ? shi[warp][g] : 0;
+        gl[g] = (uint32_t)g < G ? slen[warp][g] : 0;
+    }
+    // software pipeline: registers hold every group's next block while this one is solved
+    uint64_t nc0[kBsGroups], nc1[kBsGroups];
+    uint32_t ny0[kBsGroups], ny1[kBsGroups];
+#pragma unroll
+    for (int g = 0; g < kBsGroups; ++g) {
+        nc0[g] = nc1[g] = 0;
+        ny0[g] = ny1[g] = 0;
+        if (gl[g] > 0) {
+            const uint64_t s0 = (gh[g] - 1) << 6;
+            nc0[g] = Cg[s0 + lane];
+            nc1[g] = Cg[s0 + lane + 32];
+            ny0[g] = Yg[s0 + lane];
+            ny1[g] = Yg[s0 + lane + 32];
+        }
+    }
+    uint64_t T = 0;
+    for (uint32_t t = 0; t < maxlen; ++t) {
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < kBsGroups; ++g) {
+            if (t < gl[g]) {
+                sc[warp][g][lane] = nc0[g] >> 1;
+                sc[warp][g][lane + 32] = nc1[g] >> 1;
+                sy[warp][g][lane] = ny0[g];
+                sy[warp][g][lane + 32] = ny1[g];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < kBsGroups; ++g) {
+            if (t + 1 < gl[g]) {
+                const uint64_t s0 = (gh[g] - 2 - t) << 6;
+                nc0[g] = Cg[s0 + lane];
+                nc1[g] = Cg[s0 + lane + 32];
+                ny0[g] = Yg[s0 + lane];
+                ny1[g] = Yg[s0 + lane + 32];
+            }
+        }
+        if (t < len) {
+            const uint64_t *c = sc[warp][q];
+            const uint32_t *yv = sy[warp][q];
+#pragma unroll 4
+            for (int g = 15; g >= 0; --g) {
+                const int i = 4 * g + 3;
+                const uint64_t c0 = c[i], c1 = c[i - 1], c2 = c[i - 2], c3 = c[i - 3];
+                const uint32_t a0 = ((yv[i] >> k) & 1u) ^ parity64(c0 & T);
+                const uint32_t a1 = ((yv[i - 1] >> k) & 1u) ^ parity64((c1 >> 1) & T);
+                const uint32_t a2 = ((yv[i - 2] >> k) & 1u) ^ parity64((c2 >> 2) & T);
+                const uint32_t a3 = ((yv[i - 3] >> k) & 1u) ^ parity64((c3 >> 3) & T);
+                const uint32_t l1 = (uint32_t)c1, l2 = (uint32_t)c2, l3 = (uint32_t)c3;
+                const uint32_t z0 = a0;
+                const uint32_t z1 = a1 ^ (l1 & z0);
+                const uint32_t z2 = a2 ^ ((l2 >> 1) & z0) ^ (l2 & z1);
+                const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
+                T = (T << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
+            }
+            Z[(bhi - 1 - t) * R + k] = T;
+        }
+    }
+}
+
 template <typename V>
 cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, const uint32_t *bstart,
                       uint64_t *Cg, V *Yg, uint64_t *thresh, uint8_t *texact, uint64_t *bkeys, V *bvals,
@@ -677,10 +783,14 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
     const uint64_t parts = bv ? bv->nparts : L.K;
     const unsigned grid = (unsigned)((parts + kBandWarps - 1) / kBandWarps);
     // the threshold mode is one for the whole launch (a batch shares its parameters)
-    if (L.mode == BURR_THRESH_1PLUS && !L.fallback)
+    cudaError_t e;
+    if (L.mode == BURR_THRESH_1PLUS && !L.fallback) {
+        if ((e = prefer_shared(k_band<V, true>)) != cudaSuccess) return e;
         k_band<V, true><<<grid, 32 * kBandWarps, 0, st>>>(a);
-    else
+    } else {
+        if ((e = prefer_shared(k_band<V, false>)) != cudaSuccess) return e;
         k_band<V, false><<<grid, 32 * kBandWarps, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -708,8 +818,28 @@ cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *
                            uint64_t *Z, cudaStream_t st, const BatchView *bv) {
     const uint64_t parts = bv ? bv->nparts : L.K;
     if (parts == 0) return cudaSuccess;
-    const BatchView v = bv ? *bv : BatchView();
+    if (!bv) {
+        // one structure: several partitions per warp
+        const uint32_t G = std::min<uint32_t>(32u / L.r, (uint32_t)kBsGroups);
+        const uint64_t warps = (parts + G - 1) / G;
+        const unsigned grid = (unsigned)((warps + kBsWarps - 1) / kBsWarps);
+        cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub_multi<uint8_t>)
+                        : vbytes == 2 ? prefer_shared(k_backsub_multi<uint16_t>)
+                                      : prefer_shared(k_backsub_multi<uint32_t>);
+        if (e != cudaSuccess) return e;
+        switch (vbytes) {
+        case 1: k_backsub_multi<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, G); break;
+        case 2: k_backsub_multi<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, G); break;
+        default: k_backsub_multi<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, G); break;
+        }
+        return cudaGetLastError();
+    }
+    const BatchView v = *bv;
     const unsigned grid = (unsigned)((parts + kBsWarps - 1) / kBsWarps);
+    cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub<uint8_t>)
+                    : vbytes == 2 ? prefer_shared(k_backsub<uint16_t>)
+                                  : prefer_shared(k_backsub<uint32_t>);
+    if (e != cudaSuccess) return e;
     switch (vbytes) {
     case 1: k_backsub<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, v); break;
     case 2: k_backsub<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, v); break;

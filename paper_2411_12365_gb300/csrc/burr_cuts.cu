@@ -84,6 +84,8 @@ cudaError_t launch_cut_search(const LayerDesc &L, const uint64_t *sorted_keys, c
     if (parts == 0) return cudaSuccess;
     const BatchView v = bv ? *bv : BatchView();
     const unsigned grid = (unsigned)((parts + kCutWarps - 1) / kCutWarps);
+    const cudaError_t e = prefer_shared(k_cut_search);
+    if (e != cudaSuccess) return e;
     k_cut_search<<<grid, 32 * kCutWarps, 0, st>>>(L, sorted_keys, bucket_start, mode, range, cuts, v);
     return cudaGetLastError();
 }

@@ -150,6 +150,17 @@ struct QueryDesc {
     const uint64_t *z[BURR_MAX_LAYERS + 1];   // [layers] = base case
 };
 
+// Every build kernel asks for the largest shared-memory carve-out.  Kernels of
+// different stages run side by side (back-substitution overlaps the next
+// layer's sort and band), and an SM set up for a small shared-memory share
+// must drain before a kernel that needs a larger one can start on it: with
+// mixed carve-outs the next layer waited for the whole back-substitution.
+template <typename K>
+inline cudaError_t prefer_shared(K *kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // 1+-bit threshold storage of one structure layer inside a launch: its
 // buckets in the band's exact-threshold array, its flag words and its
 // directory blocks (512 buckets each) in the launch-wide arrays.

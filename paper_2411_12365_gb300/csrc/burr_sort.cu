@@ -349,6 +349,10 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_group_sort<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
     if (e != cudaSuccess) return e;
+    if ((e = prefer_shared(k_hist)) != cudaSuccess || (e = prefer_shared(k_scan)) != cudaSuccess ||
+        (e = prefer_shared(k_scatter<V, false>)) != cudaSuccess || (e = prefer_shared(k_scatter<V, true>)) != cudaSuccess ||
+        (e = prefer_shared(k_hist_seg)) != cudaSuccess || (e = prefer_shared(k_group_sort<V>)) != cudaSuccess)
+        return e;
 
     const uint32_t *goff;
     const uint64_t *gk = keys;   // input of the group pass
@@ -548,6 +552,9 @@ cudaError_t sort_batch_impl(const BatchView &bv, const uint64_t *keys, const V *
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counts, 0, (size_t)bv.ngroups * 4, st);
     if (e != cudaSuccess) return e;
+    if ((e = prefer_shared(k_hist_batch)) != cudaSuccess || (e = prefer_shared(k_scan)) != cudaSuccess ||
+        (e = prefer_shared(k_scatter_batch<V>)) != cudaSuccess || (e = prefer_shared(k_group_sort_batch<V>)) != cudaSuccess)
+        return e;
     k_hist_batch<<<bv.ntiles, kHistThreads, 0, st>>>(keys, bv, gshift, counts);
     k_scan<<<1, 1024, 0, st>>>(counts, bv.ngroups, goff, cursor);
     k_scatter_batch<V><<<bv.ntiles, kTileThreads, tile_smem, st>>>(keys, vals, bv, gshift, cursor, tk, tv);

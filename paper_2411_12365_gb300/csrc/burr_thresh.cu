@@ -111,6 +111,8 @@ k_tcompact(const uint8_t *__restrict__ texact, const ThreshSeg *__restrict__ seg
 cudaError_t launch_thresh_flags(const uint8_t *texact, const ThreshSeg *segs, const uint32_t *blk_seg, uint32_t nblk,
                                 uint64_t *flags, uint32_t *counts, uint32_t *dir, cudaStream_t st) {
     if (nblk == 0) return cudaMemsetAsync(dir, 0, 4, st);
+    cudaError_t e;
+    if ((e = prefer_shared(k_tflags)) != cudaSuccess || (e = prefer_shared(k_tscan)) != cudaSuccess) return e;
     k_tflags<<<nblk, kThreads, 0, st>>>(texact, segs, blk_seg, flags, counts);
     k_tscan<<<1, 1024, 0, st>>>(counts, nblk, dir);
     return cudaGetLastError();
@@ -120,6 +122,8 @@ cudaError_t launch_thresh_compact(const uint8_t *texact, const ThreshSeg *segs, 
                                   uint32_t nblk, const uint64_t *flags, const uint32_t *dir, uint8_t *bytes,
                                   cudaStream_t st) {
     if (nblk == 0) return cudaSuccess;
+    const cudaError_t e = prefer_shared(k_tcompact);
+    if (e != cudaSuccess) return e;
     k_tcompact<<<nblk, kThreads, 0, st>>>(texact, segs, blk_seg, flags, dir, bytes);
     return cudaGetLastError();
 }
