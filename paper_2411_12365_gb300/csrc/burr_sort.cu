@@ -34,6 +34,7 @@ constexpr int kTile = kTileThreads * kTileItems; // 2048 keys per tile (63 regis
 constexpr uint32_t kMaxDigits = 1024;           // digits of one scatter pass
 constexpr int kGroupThreads = 512;
 constexpr uint32_t kGroupCap = 12288;           // keys a group may hold to be sorted in shared memory
+constexpr int kUnroll = 8;                      // keys in flight per thread in the counting loops
 
 inline uint32_t ceil_log2(uint64_t x) {
     uint32_t l = 0;
@@ -101,8 +102,15 @@ k_hist(const uint64_t *__restrict__ keys, uint64_t n, uint64_t sigma, uint64_t r
     for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) >> dshift], 1u);
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
+        uint64_t k[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * stride];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) atomicAdd(&sh[group_of(k[j], sigma, range, gshift) >> dshift], 1u);
+    }
+    for (; i < n; i += stride) atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) >> dshift], 1u);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < D; i += blockDim.x)
         if (sh[i]) atomicAdd(&counts[i], sh[i]);
@@ -117,8 +125,16 @@ k_hist_seg(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ off1,
     for (uint32_t i = threadIdx.x; i < D2; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint32_t lo = off1[seg], hi = off1[seg + 1];
-    for (uint32_t i = lo + part * blockDim.x + threadIdx.x; i < hi; i += nseg_ctas * blockDim.x)
-        atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) & (D2 - 1)], 1u);
+    const uint32_t stride = nseg_ctas * blockDim.x;
+    uint32_t i = lo + part * blockDim.x + threadIdx.x;
+    for (; (uint64_t)i + (kUnroll - 1) * (uint64_t)stride < hi; i += kUnroll * stride) {
+        uint64_t k[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * stride];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) atomicAdd(&sh[group_of(k[j], sigma, range, gshift) & (D2 - 1)], 1u);
+    }
+    for (; i < hi; i += stride) atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) & (D2 - 1)], 1u);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < D2; i += blockDim.x)
         if (sh[i]) atomicAdd(&counts[(uint64_t)seg * D2 + i], sh[i]);
@@ -281,15 +297,43 @@ k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, cons
     const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
     if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    {
+        uint32_t i = lo + threadIdx.x;
+        for (; (uint64_t)i + (kUnroll - 1) * (uint64_t)blockDim.x < hi; i += kUnroll * blockDim.x) {
+            uint64_t k[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * blockDim.x];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j)
+                atomicAdd(&cnt[(start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+        }
+        for (; i < hi; i += blockDim.x)
+            atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    }
     __syncthreads();
     block_scan(cnt, cur, kGroupBuckets, warp_sums);
     if (threadIdx.x < nbk) bucket_start[b_lo + threadIdx.x] = lo + cur[threadIdx.x];
     if (g == gridDim.x - 1 && threadIdx.x == 0) bucket_start[nb] = hi;
     __syncthreads();
     if (n <= kGroupCap) {
-        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        uint32_t i = lo + threadIdx.x;
+        for (; (uint64_t)i + 3 * (uint64_t)blockDim.x < hi; i += 4 * blockDim.x) {
+            uint64_t k[4];
+            V v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                k[j] = keys[i + j * blockDim.x];
+                v[j] = vals[i + j * blockDim.x];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t b = (start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo;
+                const uint32_t p = atomicAdd(&cur[b], 1u);
+                skey[p] = k[j];
+                sval[p] = v[j];
+            }
+        }
+        for (; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
             const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
             const uint32_t p = atomicAdd(&cur[b], 1u);
@@ -501,15 +545,43 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
     const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
     if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    {
+        uint32_t i = lo + threadIdx.x;
+        for (; (uint64_t)i + (kUnroll - 1) * (uint64_t)blockDim.x < hi; i += kUnroll * blockDim.x) {
+            uint64_t k[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * blockDim.x];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j)
+                atomicAdd(&cnt[(start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+        }
+        for (; i < hi; i += blockDim.x)
+            atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+    }
     __syncthreads();
     block_scan(cnt, cur, kGroupBuckets, warp_sums);
     if (threadIdx.x < nbk) bucket_start[D.bucket_base + b_lo + threadIdx.x] = lo + cur[threadIdx.x];
     if (g == gridDim.x - 1 && threadIdx.x == 0) bucket_start[bv.nbuckets] = hi;
     __syncthreads();
     if (n <= kGroupCap) {
-        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        uint32_t i = lo + threadIdx.x;
+        for (; (uint64_t)i + 3 * (uint64_t)blockDim.x < hi; i += 4 * blockDim.x) {
+            uint64_t k[4];
+            V v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                k[j] = keys[i + j * blockDim.x];
+                v[j] = vals[i + j * blockDim.x];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t b = (start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo;
+                const uint32_t p = atomicAdd(&cur[b], 1u);
+                skey[p] = k[j];
+                sval[p] = v[j];
+            }
+        }
+        for (; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
             const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
             const uint32_t p = atomicAdd(&cur[b], 1u);
