@@ -205,10 +205,6 @@ __device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, un
                  : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.L2 [%0];" ::"l"(p));
-}
-
 // Plain 128-bit read of a ring slot.  A slot goes from empty to its final
 // contents once per set (one atomic write), so a read that sees a nonzero row
 // and a valid right-hand side has seen a stored equation that stays; any

@@ -150,6 +150,11 @@ struct QueryDesc {
     const uint64_t *z[BURR_MAX_LAYERS + 1];   // [layers] = base case
 };
 
+// Ask for the line holding p to be brought into L2 (no registers, no wait).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.L2 [%0];" ::"l"(p));
+}
+
 // Every build kernel asks for the largest shared-memory carve-out.  Kernels of
 // different stages run side by side (back-substitution overlaps the next
 // layer's sort and band), and an SM set up for a small shared-memory share

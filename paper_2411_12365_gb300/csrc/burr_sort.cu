@@ -211,7 +211,7 @@ __device__ void block_scan(const uint32_t *cnt, uint32_t *out, uint32_t len, uin
 // stay inside pass-1 bin seg = blockIdx / nseg_ctas, digit = group & (D - 1),
 // cursor[seg * D + digit] (= cursor[group]).
 template <typename V, bool SEG>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 4)
 k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
           const uint32_t *__restrict__ off1, uint32_t nseg_ctas, uint64_t sigma, uint64_t range, uint32_t gshift,
           uint32_t dshift, uint32_t D, uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out,
@@ -237,6 +237,19 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
     for (uint64_t t = part; t < ntiles; t += nparts) {
         const uint64_t base = lo + t * kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)kTile, hi - base);
+        // the CTA's next tile is brought into L2 while this one is worked on
+        if (t + nparts < ntiles) {
+            const uint64_t nbase = lo + (t + nparts) * kTile;
+            const uint32_t ncnt = (uint32_t)min((uint64_t)kTile, hi - nbase);
+            constexpr uint32_t kKeyLines = kTile * 8 / 128;
+            if (threadIdx.x < kKeyLines) {
+                const uint32_t o = threadIdx.x * (128 / 8);
+                if (o < ncnt) prefetch_l2(keys + nbase + o);
+            } else if (threadIdx.x < kKeyLines + kTile * sizeof(V) / 128) {
+                const uint32_t o = (threadIdx.x - kKeyLines) * (uint32_t)(128 / sizeof(V));
+                if (o < ncnt) prefetch_l2(vals + nbase + o);
+            }
+        }
         uint64_t key[kTileItems];
         V val[kTileItems];
         uint32_t dig[kTileItems], rank[kTileItems];
@@ -252,9 +265,20 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
             }
         }
         __syncthreads();
+        // reserve the tile's output ranges first; the atomics' round trip overlaps the scan
+        uint32_t res[kMaxDigits / kTileThreads];
+#pragma unroll
+        for (int k = 0; k < (int)(kMaxDigits / kTileThreads); ++k) {
+            const uint32_t d = threadIdx.x + (uint32_t)k * kTileThreads;
+            res[k] = 0;
+            if (d < D && hist[d]) res[k] = atomicAdd(&cursor[(uint64_t)seg * (SEG ? D : 0) + d], hist[d]);
+        }
         block_scan(hist, excl, D, warp_sums);
-        for (uint32_t d = threadIdx.x; d < D; d += blockDim.x)
-            if (hist[d]) gbase[d] = atomicAdd(&cursor[(uint64_t)seg * (SEG ? D : 0) + d], hist[d]);
+#pragma unroll
+        for (int k = 0; k < (int)(kMaxDigits / kTileThreads); ++k) {
+            const uint32_t d = threadIdx.x + (uint32_t)k * kTileThreads;
+            if (d < D) gbase[d] = res[k];
+        }
 #pragma unroll
         for (int j = 0; j < kTileItems; ++j) {
             const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
