@@ -583,79 +583,12 @@ __device__ __forceinline__ uint32_t parity64(uint64_t x) {
     return (uint32_t)__popc((uint32_t)x ^ (uint32_t)(x >> 32)) & 1u;
 }
 
-template <typename V>
-__global__ void __launch_bounds__(32 * kBsWarps)
-k_backsub(LayerDesc L0, const uint64_t *__restrict__ Cg0, const V *__restrict__ Yg0, uint64_t *__restrict__ Z0,
-          BatchView bv) {
-    __shared__ uint64_t sc[kBsWarps][64];
-    __shared__ uint32_t sy[kBsWarps][64];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t gp = (uint64_t)blockIdx.x * kBsWarps + warp;
-    LayerDesc L;
-    uint64_t part;
-    const uint64_t *Cg = Cg0;
-    const V *Yg = Yg0;
-    uint64_t *Z = Z0;
-    if (bv.sd) {
-        if (gp >= bv.nparts) return;
-        const StructDesc &D = bv.sd[bv.part_struct[gp]];
-        L = D.L;
-        part = gp - D.part_base;
-        Cg += D.slot_base;
-        Yg += D.slot_base;
-        Z += D.z_base;
-    } else {
-        L = L0;
-        part = gp;
-    }
-    if (part >= L.K) return;
-    const uint64_t own_lo = part_own_lo(L, part);
-    const uint64_t own_hi = part_own_hi(L, part);
-    const uint64_t blo = own_lo >> 6, bhi = own_hi >> 6;
-    if (bhi <= blo) return;
-    uint64_t T = 0;
-    // software pipeline: registers hold the next block while this one is solved
-    uint64_t nc0 = Cg[((bhi - 1) << 6) + lane], nc1 = Cg[((bhi - 1) << 6) + lane + 32];
-    uint32_t ny0 = Yg[((bhi - 1) << 6) + lane], ny1 = Yg[((bhi - 1) << 6) + lane + 32];
-    for (uint64_t blk = bhi; blk-- > blo;) {
-        __syncwarp();
-        sc[warp][lane] = nc0 >> 1;
-        sc[warp][lane + 32] = nc1 >> 1;
-        sy[warp][lane] = ny0;
-        sy[warp][lane + 32] = ny1;
-        __syncwarp();
-        if (blk > blo) {
-            const uint64_t s0 = (blk - 1) << 6;
-            nc0 = Cg[s0 + lane];
-            nc1 = Cg[s0 + lane + 32];
-            ny0 = Yg[s0 + lane];
-            ny1 = Yg[s0 + lane + 32];
-        }
-        if ((uint32_t)lane < L.r) {
-#pragma unroll 4
-            for (int g = 15; g >= 0; --g) {
-                const int i = 4 * g + 3;
-                const uint64_t c0 = sc[warp][i], c1 = sc[warp][i - 1], c2 = sc[warp][i - 2], c3 = sc[warp][i - 3];
-                const uint32_t a0 = ((sy[warp][i] >> lane) & 1u) ^ parity64(c0 & T);
-                const uint32_t a1 = ((sy[warp][i - 1] >> lane) & 1u) ^ parity64((c1 >> 1) & T);
-                const uint32_t a2 = ((sy[warp][i - 2] >> lane) & 1u) ^ parity64((c2 >> 2) & T);
-                const uint32_t a3 = ((sy[warp][i - 3] >> lane) & 1u) ^ parity64((c3 >> 3) & T);
-                const uint32_t l1 = (uint32_t)c1, l2 = (uint32_t)c2, l3 = (uint32_t)c3;
-                const uint32_t z0 = a0;
-                const uint32_t z1 = a1 ^ (l1 & z0);
-                const uint32_t z2 = a2 ^ ((l2 >> 1) & z0) ^ (l2 & z1);
-                const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
-                T = (T << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
-            }
-            Z[blk * L.r + lane] = T;
-        }
-    }
-}
-
-// Back-substitution of a single structure's layer with several partitions per
-// warp: a partition needs only r lanes (one per bit plane), so the warp solves
-// G = min(32 / r, kBsGroups) partitions side by side, lanes [q*r, q*r + r) on
-// partition q.  The arithmetic is that of k_backsub; sharing each instruction
+// Back-substitution with several partitions per warp: a partition needs only
+// r lanes (one per bit plane), so a warp solves G = min(32 / R, kBsGroups)
+// partitions side by side, lanes [q*R, q*R + R) on partition q, where R is an
+// upper bound of r over the launch (r itself for one structure, 8 x value bytes
+// for a batch, whose structures may differ in r; lanes past a structure's r
+// sit out).  Each group runs the four-slot steps above; sharing each instruction
 // among G partitions cuts the issue load G-fold, which matters because the
 // solve runs beside the next layer's sort and band.  Partitions of one warp may
 // differ in length: each walks its own blocks from the right, and a finished
@@ -664,37 +597,54 @@ constexpr int kBsGroups = 8;
 
 template <typename V>
 __global__ void __launch_bounds__(32 * kBsWarps)
-k_backsub_multi(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z,
-                uint32_t G) {
+k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z0,
+                BatchView bv, uint32_t R, uint32_t G) {
     __shared__ uint64_t sc[kBsWarps][kBsGroups][64];
     __shared__ uint32_t sy[kBsWarps][kBsGroups][64];
-    __shared__ uint64_t shi[kBsWarps][kBsGroups];   // one past the last block of each group's partition
-    __shared__ uint32_t slen[kBsWarps][kBsGroups];  // its number of blocks
+    __shared__ uint64_t sbase[kBsWarps][kBsGroups];  // first slot of the group's structure in the layer arrays
+    __shared__ uint64_t shi[kBsWarps][kBsGroups];    // one past the last block of the group's partition
+    __shared__ uint32_t slen[kBsWarps][kBsGroups];   // its number of blocks
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t R = L.r;
     const uint32_t q = (uint32_t)lane / R, k = (uint32_t)lane % R;
-    const uint64_t part0 = ((uint64_t)blockIdx.x * kBsWarps + warp) * G;
-    uint64_t bhi = 0;
-    uint32_t len = 0;
-    if (q < G && part0 + q < L.K) {
-        const uint64_t lo = part_own_lo(L, part0 + q) >> 6, hi = part_own_hi(L, part0 + q) >> 6;
+    const uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q;
+    const uint64_t nparts = bv.sd ? bv.nparts : L0.K;
+    uint64_t bhi = 0, base = 0;
+    uint32_t len = 0, r = 0;
+    uint64_t *Z = Z0;
+    if (q < G && gp < nparts) {
+        LayerDesc L;
+        uint64_t part;
+        if (bv.sd) {
+            const StructDesc &D = bv.sd[bv.part_struct[gp]];
+            L = D.L;
+            part = gp - D.part_base;
+            base = D.slot_base;
+            Z += D.z_base;
+        } else {
+            L = L0;
+            part = gp;
+        }
+        const uint64_t lo = part_own_lo(L, part) >> 6, hi = part_own_hi(L, part) >> 6;
         if (hi > lo) {
             bhi = hi;
             len = (uint32_t)(hi - lo);
         }
+        r = L.r;
     }
     if (q < G && k == 0) {
+        sbase[warp][q] = base;
         shi[warp][q] = bhi;
         slen[warp][q] = len;
     }
     const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
     __syncwarp();
     if (maxlen == 0) return;
-    uint64_t gh[kBsGroups];
+    uint64_t gh[kBsGroups], gb[kBsGroups];
     uint32_t gl[kBsGroups];
 #pragma unroll
     for (int g = 0; g < kBsGroups; ++g) {
         gh[g] = (uint32_t)g < G ? shi[warp][g] : 0;
+        gb[g] = (uint32_t)g < G ? sbase[warp][g] : 0;
         gl[g] = (uint32_t)g < G ? slen[warp][g] : 0;
     }
     // software pipeline: registers hold every group's next block while this one is solved
@@ -705,13 +655,14 @@ k_backsub_multi(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restric
         nc0[g] = nc1[g] = 0;
         ny0[g] = ny1[g] = 0;
         if (gl[g] > 0) {
-            const uint64_t s0 = (gh[g] - 1) << 6;
+            const uint64_t s0 = gb[g] + ((gh[g] - 1) << 6);
             nc0[g] = Cg[s0 + lane];
             nc1[g] = Cg[s0 + lane + 32];
             ny0[g] = Yg[s0 + lane];
             ny1[g] = Yg[s0 + lane + 32];
         }
     }
+    const bool solve = k < r;
     uint64_t T = 0;
     for (uint32_t t = 0; t < maxlen; ++t) {
         __syncwarp();
@@ -728,14 +679,14 @@ k_backsub_multi(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restric
 #pragma unroll
         for (int g = 0; g < kBsGroups; ++g) {
             if (t + 1 < gl[g]) {
-                const uint64_t s0 = (gh[g] - 2 - t) << 6;
+                const uint64_t s0 = gb[g] + ((gh[g] - 2 - t) << 6);
                 nc0[g] = Cg[s0 + lane];
                 nc1[g] = Cg[s0 + lane + 32];
                 ny0[g] = Yg[s0 + lane];
                 ny1[g] = Yg[s0 + lane + 32];
             }
         }
-        if (t < len) {
+        if (solve && t < len) {
             const uint64_t *c = sc[warp][q];
             const uint32_t *yv = sy[warp][q];
 #pragma unroll 4
@@ -753,7 +704,7 @@ k_backsub_multi(LayerDesc L, const uint64_t *__restrict__ Cg, const V *__restric
                 const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
                 T = (T << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
             }
-            Z[(bhi - 1 - t) * R + k] = T;
+            Z[(bhi - 1 - t) * r + k] = T;
         }
     }
 }
@@ -814,32 +765,20 @@ cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *
                            uint64_t *Z, cudaStream_t st, const BatchView *bv) {
     const uint64_t parts = bv ? bv->nparts : L.K;
     if (parts == 0) return cudaSuccess;
-    if (!bv) {
-        // one structure: several partitions per warp
-        const uint32_t G = std::min<uint32_t>(32u / L.r, (uint32_t)kBsGroups);
-        const uint64_t warps = (parts + G - 1) / G;
-        const unsigned grid = (unsigned)((warps + kBsWarps - 1) / kBsWarps);
-        cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub_multi<uint8_t>)
-                        : vbytes == 2 ? prefer_shared(k_backsub_multi<uint16_t>)
-                                      : prefer_shared(k_backsub_multi<uint32_t>);
-        if (e != cudaSuccess) return e;
-        switch (vbytes) {
-        case 1: k_backsub_multi<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, G); break;
-        case 2: k_backsub_multi<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, G); break;
-        default: k_backsub_multi<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, G); break;
-        }
-        return cudaGetLastError();
-    }
-    const BatchView v = *bv;
-    const unsigned grid = (unsigned)((parts + kBsWarps - 1) / kBsWarps);
-    cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub<uint8_t>)
-                    : vbytes == 2 ? prefer_shared(k_backsub<uint16_t>)
-                                  : prefer_shared(k_backsub<uint32_t>);
+    // several partitions per warp; a batch's structures may differ in r (up to 8 bits per value byte)
+    const uint32_t R = bv ? 8u * vbytes : L.r;
+    const uint32_t G = std::min<uint32_t>(32u / R, (uint32_t)kBsGroups);
+    const uint64_t warps = (parts + G - 1) / G;
+    const unsigned grid = (unsigned)((warps + kBsWarps - 1) / kBsWarps);
+    const BatchView v = bv ? *bv : BatchView();
+    cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub_multi<uint8_t>)
+                    : vbytes == 2 ? prefer_shared(k_backsub_multi<uint16_t>)
+                                  : prefer_shared(k_backsub_multi<uint32_t>);
     if (e != cudaSuccess) return e;
     switch (vbytes) {
-    case 1: k_backsub<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, v); break;
-    case 2: k_backsub<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, v); break;
-    default: k_backsub<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, v); break;
+    case 1: k_backsub_multi<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, v, R, G); break;
+    case 2: k_backsub_multi<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, v, R, G); break;
+    default: k_backsub_multi<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, v, R, G); break;
     }
     return cudaGetLastError();
 }
