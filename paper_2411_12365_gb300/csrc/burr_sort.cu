@@ -210,6 +210,37 @@ __device__ void block_scan(const uint32_t *cnt, uint32_t *out, uint32_t len, uin
 // group >> dshift over all n keys, cursor[digit].  Segmented (pass 2): tiles
 // stay inside pass-1 bin seg = blockIdx / nseg_ctas, digit = group & (D - 1),
 // cursor[seg * D + digit] (= cursor[group]).
+// Asynchronous global -> shared copies (the tile loads of k_scatter).
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared memory of k_scatter: the ordered tile (keys, values, digits) and the
+// input buffer the next tile is copied into while this one is worked on.
+template <typename V>
+constexpr size_t scatter_smem_bytes() {
+    return (((size_t)kTile * (8 + sizeof(V) + 2) + 15) & ~(size_t)15) + (size_t)kTile * 8 + (size_t)kTile * sizeof(V) + 8;
+}
+
+// One scatter pass.  Tiles of kTile keys are ordered by digit in shared
+// memory and written as contiguous runs.  Unsegmented (pass 1): digit =
+// group >> dshift over all n keys, cursor[digit].  Segmented (pass 2): tiles
+// stay inside pass-1 bin seg = blockIdx / nseg_ctas, digit = group & (D - 1),
+// cursor[seg * D + digit] (= cursor[group]).
+//
+// A CTA copies its next tile into shared memory asynchronously (cp.async)
+// while it orders and writes the current one, so the load latency overlaps
+// the work.  Keys go in 8-byte copies.  Values go in 4-byte chunks from the
+// aligned-down address, when the array starts on 4 bytes and the rounded-up
+// end of the tile stays inside it; otherwise the tile's values are read
+// directly when it is worked on.
 template <typename V, bool SEG>
 __global__ void __launch_bounds__(kTileThreads, 4)
 k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
@@ -220,6 +251,8 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
     V *sval = reinterpret_cast<V *>(skey + kTile);
     uint16_t *sdig = reinterpret_cast<uint16_t *>(sval + kTile);
+    uint64_t *ikey = reinterpret_cast<uint64_t *>(smem_raw + (((size_t)kTile * (8 + sizeof(V) + 2) + 15) & ~(size_t)15));
+    unsigned char *ival = reinterpret_cast<unsigned char *>(ikey + kTile);
     __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
 
     uint64_t lo = 0, hi = n;
@@ -231,34 +264,49 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
         lo = off1[seg];
         hi = off1[seg + 1];
     }
+    const bool vals_aligned = ((uintptr_t)vals & 3u) == 0;
+    // start the copy of tile t into the input buffer; returns whether its values are copied too
+    auto issue = [&](uint64_t t) -> bool {
+        const uint64_t base = lo + t * kTile;
+        const uint32_t cnt = (uint32_t)min((uint64_t)kTile, hi - base);
+        for (uint32_t i = threadIdx.x; i < cnt; i += kTileThreads) cp_async8(ikey + i, keys + base + i);
+        const uint64_t b0 = base * sizeof(V), a0 = b0 & ~3ull, a1 = ((base + cnt) * sizeof(V) + 3) & ~3ull;
+        const bool va = vals_aligned && a1 <= n * sizeof(V);
+        if (va) {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(vals) + a0;
+            const uint32_t nchunks = (uint32_t)((a1 - a0) >> 2);
+            for (uint32_t c = threadIdx.x; c < nchunks; c += kTileThreads) cp_async4(ival + 4 * c, src + 4 * c);
+        }
+        cp_async_commit();
+        return va;
+    };
     for (uint32_t i = threadIdx.x; i < D; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
     const uint64_t ntiles = (hi - lo + kTile - 1) / kTile;
+    bool va = part < ntiles ? issue(part) : false;
+    __syncthreads();
     for (uint64_t t = part; t < ntiles; t += nparts) {
         const uint64_t base = lo + t * kTile;
         const uint32_t cnt = (uint32_t)min((uint64_t)kTile, hi - base);
-        // the CTA's next tile is brought into L2 while this one is worked on
-        if (t + nparts < ntiles) {
-            const uint64_t nbase = lo + (t + nparts) * kTile;
-            const uint32_t ncnt = (uint32_t)min((uint64_t)kTile, hi - nbase);
-            constexpr uint32_t kKeyLines = kTile * 8 / 128;
-            if (threadIdx.x < kKeyLines) {
-                const uint32_t o = threadIdx.x * (128 / 8);
-                if (o < ncnt) prefetch_l2(keys + nbase + o);
-            } else if (threadIdx.x < kKeyLines + kTile * sizeof(V) / 128) {
-                const uint32_t o = (threadIdx.x - kKeyLines) * (uint32_t)(128 / sizeof(V));
-                if (o < ncnt) prefetch_l2(vals + nbase + o);
-            }
-        }
+        cp_async_wait_all();
+        __syncthreads();
         uint64_t key[kTileItems];
         V val[kTileItems];
         uint32_t dig[kTileItems], rank[kTileItems];
+        const uint32_t vshift = (uint32_t)((base * sizeof(V)) & 3u);
 #pragma unroll
         for (int j = 0; j < kTileItems; ++j) {
             const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
             if (i < cnt) {
-                key[j] = keys[base + i];
-                val[j] = vals[base + i];
+                key[j] = ikey[i];
+                val[j] = va ? *reinterpret_cast<const V *>(ival + vshift + i * sizeof(V)) : vals[base + i];
+            }
+        }
+        __syncthreads();   // the input buffer is free: copy the next tile while this one is worked on
+        const bool va_next = t + nparts < ntiles ? issue(t + nparts) : false;
+#pragma unroll
+        for (int j = 0; j < kTileItems; ++j) {
+            const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
+            if (i < cnt) {
                 const uint32_t g = group_of(key[j], sigma, range, gshift);
                 dig[j] = SEG ? (g & (D - 1)) : (g >> dshift);
                 rank[j] = atomicAdd(&hist[dig[j]], 1u);
@@ -298,8 +346,9 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
         }
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < D; d += blockDim.x) hist[d] = 0;
-        __syncthreads();
+        va = va_next;
     }
+    cp_async_wait_all();
 }
 
 // Last pass: one block per group of 64 buckets.  The group's keys are
@@ -408,7 +457,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
     const Plan P = make_plan(L);
     Scratch S = carve(scratch, n, P.ngroups, sizeof(V));
     const unsigned sms = (unsigned)num_sms();
-    const size_t tile_smem = (size_t)kTile * (8 + sizeof(V) + 2);
+    const size_t tile_smem = scatter_smem_bytes<V>();
     const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
     cudaError_t e;
     e = cudaFuncSetAttribute(k_scatter<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
