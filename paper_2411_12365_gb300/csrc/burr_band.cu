@@ -51,7 +51,13 @@ constexpr int kRing = 512;
 constexpr uint32_t kRingMask = kRing - 1;
 constexpr int kStage = 256;             // rows of a bucket staged at once
 constexpr int kStagePerLane = kStage / 32;
-constexpr int kBandWarps = 4;           // partitions per CTA
+// Partitions (warps) per CTA.  Small CTAs spread partitions evenly over the
+// SMs (1503 partitions at 10^8 keys fill ~10 of the 12 warp slots per SM) and
+// give a finer tail; 2 measured best against 1 and 4.
+#ifndef BURR_BAND_WARPS
+#define BURR_BAND_WARPS 2
+#endif
+constexpr int kBandWarps = BURR_BAND_WARPS;
 constexpr unsigned kFull = 0xffffffffu;
 
 constexpr unsigned long long kYValid = 1ull << 32;   // marks a stored right-hand side
