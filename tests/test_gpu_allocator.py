@@ -130,3 +130,41 @@ def test_allocation_failure_is_clean(which, kind):
         assert torch.equal(hs[0].query(keys[:1000]), vals[:1000])
     for h in hs:
         h.free()
+
+
+@pytest.mark.parametrize("r", [8, 16])
+def test_tables_off_32_byte_boundaries_take_the_narrow_query(r):
+    # A caller's allocator may return blocks that are 16-byte aligned but not
+    # 32-byte aligned.  The query then reads table windows in 8-byte loads
+    # instead of 32-byte ones; the answers and the export are unchanged.
+    keys = I.keys_torch(400_000, "cuda", seed=91)
+    vals = I.values_torch(keys, r)
+    ref = burr.build(keys, vals, r, partition_slots=8192)
+    ref_ex = ref.export()
+    want = ref.query(keys)
+    ref.free()
+    dev = torch.cuda.current_device()
+    shifted = {}
+
+    def alloc(n, stream):
+        p = torch.cuda.caching_allocator_alloc(n + 64, dev, stream)
+        q = (p + 31) // 32 * 32 + 16          # 16 bytes past a 32-byte boundary
+        shifted[q] = p
+        return q
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(shifted.pop(ptr))
+
+    burr.set_allocator(alloc, free)
+    h = None
+    try:
+        h = burr.build(keys, vals, r, partition_slots=8192)
+        assert h.export() == ref_ex
+        assert torch.equal(h.query(keys), want)
+        assert torch.equal(h.query(keys[::7]), want[::7])
+    finally:
+        if h is not None:
+            h.free()
+        torch.cuda.synchronize()
+        burr.set_allocator(None, None)
+    assert not shifted
