@@ -121,14 +121,20 @@ uint64_t or_num_buckets(uint64_t m, uint32_t w, uint32_t B)
 }
 
 /* Number of partitions of a layer with m slots (minimum-buckets-per-thread
- * analogue, Sec. 3): layers below min_slots, or smaller than two partitions,
- * are one partition; otherwise floor(m/P) partitions, the last one taking the
- * remainder.  Cut j (j >= 1) sits at start slot j*P. */
+ * analogue, Sec. 3): layers below min_slots, or smaller than P, are one
+ * partition.  Otherwise there are floor(m/P) partitions of P slots, plus one
+ * more for the remainder m mod P when it is at least
+ * T = max(min(min_slots, P/2), 1024) slots; a smaller remainder joins the
+ * last partition.  So no partition is much longer than P (the paper gives the
+ * threads near-equal shares).  Cut j (j >= 1) sits at start slot j*P. */
 uint64_t or_num_partitions(uint64_t m, uint64_t P, uint64_t min_slots)
 {
     if (m == 0) return 0;
     if (m < min_slots || m < P) return 1;
-    return m / P;
+    uint64_t T = min_slots < P / 2 ? min_slots : P / 2;
+    if (T < 1024) T = 1024;
+    uint64_t K = m / P, rem = m % P;
+    return rem >= T ? K + 1 : K;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -67,10 +67,16 @@ uint64_t layer_partition_slots(const burr_params &p, uint32_t l) {
     return (l > 0 && p.lower_partition_slots) ? p.lower_partition_slots : p.partition_slots;
 }
 
+// Partitions of a layer of m slots (Sec. 3, minimum buckets per thread): one
+// below minP slots or below P; else floor(m/P) partitions of P slots, plus one
+// for the remainder m mod P when it is at least max(min(minP, P/2), 1024)
+// slots (a smaller remainder joins the last partition).  No partition is then
+// much longer than P; the longest partition sets the band kernel's time.
 uint64_t num_partitions(uint64_t m, uint64_t P, uint64_t minP) {
     if (m == 0) return 0;
     if (m < minP || m < P) return 1;
-    return m / P;
+    const uint64_t T = std::max<uint64_t>(std::min<uint64_t>(minP, P / 2), 1024);
+    return m % P >= T ? m / P + 1 : m / P;
 }
 
 int forced_code(const uint32_t lv[4]) {
