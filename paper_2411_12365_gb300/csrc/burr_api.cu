@@ -11,6 +11,8 @@
 #include <memory>
 #include <string>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -60,6 +62,7 @@ uint64_t fallback_slots(uint64_t n, double slack, uint32_t attempt) {
 }
 
 uint64_t num_buckets(uint64_t m, uint32_t B) { return m == 0 ? 0 : (m - kW + B) / B; }
+
 
 // Partition size of bumping layer l: layer 0 is cut every partition_slots,
 // deeper layers every lower_partition_slots (0: partition_slots).
@@ -333,17 +336,24 @@ struct Timer {
 
 // A second stream for back-substitution: layer l's back-substitution does not
 // feed layer l+1 (only its bumped keys do), so it runs while layer l+1 sorts
-// and bands.  The band buffers alternate between two sets so that layer l+1
-// never overwrites the band layer l is still solving.  On destruction the
-// build stream waits for the side stream, so every later free on the build
-// stream is ordered after the side stream's reads.
+// and bands.  The band buffers rotate over three sets (layer l uses set l % 3)
+// so that neither layer l+1 nor layer l+2 overwrites the band layer l is still
+// solving: with two sets, layer l+2 waited for layer l's back-substitution,
+// which is the longest (layer 0's).  On destruction the build stream waits for
+// the side stream, so every later free on the build stream is ordered after
+// the side stream's reads.
+constexpr int kBandSets = 3;
+constexpr int kOrderSlot = kBandSets;      // event slots after the per-set ones
+constexpr int kJoinSlot = kBandSets + 1;
+constexpr int kFinalSlot = kBandSets + 2;
 struct SideStream {
     cudaStream_t main, side = nullptr;
-    cudaEvent_t ev[4] = {};
+    cudaEvent_t ev[kBandSets + 3] = {};
     explicit SideStream(cudaStream_t m) : main(m) {}
     cudaError_t init() {
         cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        for (int i = 0; i < kBandSets + 3 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
         return e;
     }
     // `to` waits for everything enqueued so far on `from`
@@ -357,7 +367,8 @@ struct SideStream {
     cudaError_t reuse(int set) { return cudaStreamWaitEvent(main, ev[set], 0); }
     ~SideStream() {
         if (side) {
-            if (ev[3] && cudaEventRecord(ev[3], side) == cudaSuccess) cudaStreamWaitEvent(main, ev[3], 0);
+            if (ev[kFinalSlot] && cudaEventRecord(ev[kFinalSlot], side) == cudaSuccess)
+                cudaStreamWaitEvent(main, ev[kFinalSlot], 0);
             cudaStreamDestroy(side);
         }
         for (auto e : ev)
@@ -403,8 +414,8 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     CK(ar.alloc(&sv, n * vb), "alloc sorted values");
     CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
     CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
-    void *cgs[2] = {nullptr, nullptr}, *ygs[2] = {nullptr, nullptr};
-    uint64_t cgcap[2] = {0, 0};
+    void *cgs[kBandSets] = {}, *ygs[kBandSets] = {};
+    uint64_t cgcap[kBandSets] = {};
     CK(ar.alloc(&cg, cap_m * 8), "alloc band");
     CK(ar.alloc(&yg, cap_m * vb), "alloc band values");
     cgs[0] = cg;
@@ -471,13 +482,13 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(ar.alloc((void **)&dc, (S.K + 1) * 4), "alloc cuts");
             L.cuts = dc;
         }
-        const int set = (int)(l & 1);
-        if (cgcap[set] < S.m) {           // second band set, sized by the first layer that uses it
+        const int set = (int)(l % kBandSets);
+        if (cgcap[set] < S.m) {           // later band sets, sized by the first layer that uses them
             CK(ar.alloc(&cgs[set], S.m * 8), "alloc band");
             CK(ar.alloc(&ygs[set], S.m * vb), "alloc band values");
             cgcap[set] = S.m;
         }
-        // the band of layer l overwrites the set that layer l-2 solved: wait for it
+        // the band of layer l overwrites the set that layer l-3 solved: wait for it
         CK(side.reuse(set), "order");
         tev[l][0] = tm.mark();
         CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
@@ -492,7 +503,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
                        S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
         tev[l][2] = tm.mark();
         if (onep) CK(launch_thresh_flags(tex, dseg, blkseg, (uint32_t)nd, S.flags, tcounts, S.dir, st), "flags");
-        CK(side.order(st, side.side, 2), "order");
+        CK(side.order(st, side.side, kOrderSlot), "order");
         tev[l][3] = tm.mark_on(side.side);
         CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side), "backsub");
         tev[l][4] = tm.mark_on(side.side);
@@ -539,7 +550,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             F.K = 1;
             F.seed_index = p.layers + a;
             F.sigma = layer_seed(p.seed, F.seed_index);
-            const int set = (int)(p.layers & 1);
+            const int set = (int)(p.layers % kBandSets);
             if (cgcap[set] < F.m) {
                 CK(ar.alloc(&cgs[set], F.m * 8), "alloc band");
                 CK(ar.alloc(&ygs[set], F.m * vb), "alloc band values");
@@ -583,7 +594,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             return fail(BURR_ERR_UNSOLVABLE, "base case unsolved after %u retries (duplicate keys?)",
                         p.fallback_max_retries);
     }
-    CK(side.order(side.side, st, 3), "order");
+    CK(side.order(side.side, st, kJoinSlot), "order");
     const int t_end = tm.mark();
     CK(cudaStreamSynchronize(st), "build");
     for (uint32_t l = 0; l <= p.layers; ++l) {
@@ -1140,7 +1151,7 @@ int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n
         if (!dk) CK(ar.alloc(&kb[i], kChunk * 8), "alloc query keys");
         if (!dout) CK(ar.alloc(&ob[i], kChunk * vb), "alloc query output");
     }
-    CK(side.order(st, side.side, 2), "order");   // the second stream starts after the allocations
+    CK(side.order(st, side.side, kOrderSlot), "order");   // the second stream starts after the allocations
     for (uint64_t c = 0, i = 0; c < n; c += kChunk, ++i) {
         const uint64_t cnt = std::min(kChunk, n - c);
         const int b = (int)(i & 1);
@@ -1156,7 +1167,7 @@ int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n
         if (!dout) CK(cudaMemcpyAsync((uint8_t *)out + c * vb, ob[b], cnt * vb, cudaMemcpyDeviceToHost, s),
                       "copy query output");
     }
-    CK(side.order(side.side, st, 3), "order");
+    CK(side.order(side.side, st, kJoinSlot), "order");
     CK(cudaStreamSynchronize(st), "query");
     return BURR_OK;
 }
@@ -1522,3 +1533,25 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Kernel attributes set once per (kernel, device, attribute, value).
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_attr_mu;
+std::set<std::tuple<const void *, int, int, int>> g_attr_set;   // kernel, device, attribute, value
+}  // namespace
+
+bool burr::attr_is_set(const void *kernel, int attr, int value) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    return g_attr_set.count(std::make_tuple(kernel, dev, attr, value)) != 0;
+}
+
+void burr::attr_mark_set(const void *kernel, int attr, int value) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    g_attr_set.insert(std::make_tuple(kernel, dev, attr, value));
+}

@@ -160,10 +160,23 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // layer's sort and band), and an SM set up for a small shared-memory share
 // must drain before a kernel that needs a larger one can start on it: with
 // mixed carve-outs the next layer waited for the whole back-substitution.
+// Kernel attributes are set once per (kernel, device, attribute, value): the
+// calls cost host time between the per-layer synchronisations, while the GPU
+// waits for the next layer's launches.
+bool attr_is_set(const void *kernel, int attr, int value);
+void attr_mark_set(const void *kernel, int attr, int value);
+
+template <typename K>
+inline cudaError_t func_attr(K *kernel, cudaFuncAttribute attr, int value) {
+    if (attr_is_set((const void *)kernel, (int)attr, value)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, attr, value);
+    if (e == cudaSuccess) attr_mark_set((const void *)kernel, (int)attr, value);
+    return e;
+}
+
 template <typename K>
 inline cudaError_t prefer_shared(K *kernel) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared);
+    return func_attr(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // 1+-bit threshold storage of one structure layer inside a launch: its

@@ -460,11 +460,11 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
     const size_t tile_smem = scatter_smem_bytes<V>();
     const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_scatter<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    e = func_attr(k_scatter<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_scatter<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    e = func_attr(k_scatter<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_group_sort<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
+    e = func_attr(k_group_sort<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
     if (e != cudaSuccess) return e;
     if ((e = prefer_shared(k_hist)) != cudaSuccess || (e = prefer_shared(k_scan)) != cudaSuccess ||
         (e = prefer_shared(k_scatter<V, false>)) != cudaSuccess || (e = prefer_shared(k_scatter<V, true>)) != cudaSuccess ||
@@ -691,9 +691,9 @@ cudaError_t sort_batch_impl(const BatchView &bv, const uint64_t *keys, const V *
     const size_t tile_smem = (size_t)kTile * (8 + sizeof(V) + 2);
     const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_scatter_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    e = func_attr(k_scatter_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_group_sort_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
+    e = func_attr(k_group_sort_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counts, 0, (size_t)bv.ngroups * 4, st);
     if (e != cudaSuccess) return e;
