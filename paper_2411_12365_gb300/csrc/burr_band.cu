@@ -444,6 +444,11 @@ __device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, con
 // kExact: 1+-bit thresholds (exact per bucket) instead of 2-bit codes; a
 // template parameter so that each mode gets its own register allocation.
 template <typename V, bool kExact>
+// The kernel needs at most 170 registers for six CTAs of two warps per SM, so
+// that all 1504 layer-0 partitions of 10^8 keys are resident at once (the
+// compiler's own choice is 166).  Measured: at 186 registers (5 CTAs per SM)
+// the layer-0 band took 15.5 ms instead of 9.7; capped at 128 registers (8
+// CTAs, with spills) 13.4 ms; capped at 168 registers 9.9 ms.
 __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
