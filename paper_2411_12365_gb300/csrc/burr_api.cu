@@ -3,6 +3,7 @@
 // export and statistics.  Every step of the method runs in the kernels of
 // burr_sort.cu, burr_band.cu and burr_query.cu; this file only sizes layers,
 // allocates, launches and reads back one counter per layer.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -635,6 +636,7 @@ uint64_t autotune_partition_slots(const std::vector<uint64_t> &n, double alpha) 
 struct BatchTables {
     std::vector<StructDesc> sd;
     std::vector<uint32_t> part_struct, group_struct, tile_struct;
+    std::vector<uint32_t> part_order;   // partitions by decreasing length (the band's launch order)
     std::vector<uint64_t> tile_lo;
     std::vector<uint32_t> who;   // active index -> structure index
     uint64_t nbuckets = 0, ngroups = 0, nparts = 0, slots = 0, tw = 0, zw = 0, nkeys = 0;
@@ -689,6 +691,16 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
         T.zw = (T.zw + 3) & ~3ull;   // every structure's table starts on 32 bytes (wide query loads)
         T.nkeys += n[s];
     }
+    // Longest partitions first: a warp's partition is one dependent chain, so
+    // the launch ends with the short ones instead of a long one started late.
+    std::vector<uint64_t> len(T.nparts);
+    for (uint32_t i = 0; i < T.sd.size(); ++i)
+        for (uint64_t k = 0; k < T.sd[i].L.K; ++k)
+            len[T.sd[i].part_base + k] = part_bucket(T.sd[i].L, k + 1) - part_bucket(T.sd[i].L, k);
+    T.part_order.resize(T.nparts);
+    for (uint32_t j = 0; j < T.nparts; ++j) T.part_order[j] = j;
+    std::stable_sort(T.part_order.begin(), T.part_order.end(),
+                     [&](uint32_t a, uint32_t b) { return len[a] > len[b]; });
     return BURR_OK;
 }
 
@@ -765,15 +777,17 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
     };
     auto view = [&](const BatchTables &T, BatchView &v) -> int {
         StructDesc *dsd;
-        uint32_t *dps, *dgs, *dts;
+        uint32_t *dps, *dpo, *dgs, *dts;
         uint64_t *dtl;
         CK(upload(ar, T.sd, &dsd, st), "upload descriptors");
         CK(upload(ar, T.part_struct, &dps, st), "upload partitions");
+        CK(upload(ar, T.part_order, &dpo, st), "upload partition order");
         CK(upload(ar, T.group_struct, &dgs, st), "upload groups");
         CK(upload(ar, T.tile_struct, &dts, st), "upload tiles");
         CK(upload(ar, T.tile_lo, &dtl, st), "upload tiles");
         v.sd = dsd;
         v.part_struct = dps;
+        v.part_order = dpo;
         v.group_struct = dgs;
         v.tile_struct = dts;
         v.tile_lo = dtl;

@@ -452,10 +452,11 @@ template <typename V, bool kExact>
 __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t gp = (uint64_t)blockIdx.x * kBandWarps + warp;
+    uint64_t gp = (uint64_t)blockIdx.x * kBandWarps + warp;
     Ctx x;
     if (a.bv.sd) {
         if (gp >= a.bv.nparts) return;
+        if (a.bv.part_order) gp = a.bv.part_order[gp];   // longest partitions first
         const uint32_t si = a.bv.part_struct[gp];
         const StructDesc &D = a.bv.sd[si];
         x.L = D.L;
@@ -621,7 +622,7 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
     __shared__ uint32_t slen[kBsWarps][kBsGroups];   // its number of blocks
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = (uint32_t)lane / R, k = (uint32_t)lane % R;
-    const uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q;
+    uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q;
     const uint64_t nparts = bv.sd ? bv.nparts : L0.K;
     uint64_t bhi = 0, base = 0;
     uint32_t len = 0, r = 0;
@@ -630,6 +631,7 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
         LayerDesc L;
         uint64_t part;
         if (bv.sd) {
+            if (bv.part_order) gp = bv.part_order[gp];   // partitions of similar length share a warp
             const StructDesc &D = bv.sd[bv.part_struct[gp]];
             L = D.L;
             part = gp - D.part_base;

@@ -94,6 +94,7 @@ struct StructDesc {
 struct BatchView {
     const StructDesc *sd = nullptr;     // per structure
     const uint32_t *part_struct = nullptr;  // global partition -> structure
+    const uint32_t *part_order = nullptr;   // launch order -> global partition (longest first); null: identity
     const uint32_t *group_struct = nullptr; // global sort group -> structure
     const uint32_t *tile_struct = nullptr;  // sort tile -> structure
     const uint64_t *tile_lo = nullptr;      // sort tile -> first key index
