@@ -274,8 +274,7 @@ def run_batched(a, ws, rank, local, pg):
     def step():
         hs = burr.build_batch(keys, vals, offs, rs, params=params)
         chosen[0] = hs[0].export()[64:72]
-        for h in hs:
-            h.free()
+        burr.free_all(hs)
 
     for _ in range(a.warmup):
         step()

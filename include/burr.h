@@ -248,6 +248,11 @@ int burr_stats(const burr_handle *h, burr_stats_t *st);
 /* Release the handle and its device memory (NULL is ignored). */
 void burr_free(burr_handle *h);
 
+/* burr_free of handles[0 .. count) in one call (NULL entries are ignored),
+ * e.g. for the handles of a batched build.  `handles` is a host array owned
+ * by the caller; the handles must not be used afterwards. */
+void burr_free_many(burr_handle *const *handles, uint64_t count);
+
 const char *burr_strerror(int code);
 const char *burr_last_error(void);
 

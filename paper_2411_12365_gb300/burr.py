@@ -66,7 +66,7 @@ class ServerStats(C.Structure):
 
 
 EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query", "burr_size_bytes", "burr_export",
-            "burr_stats", "burr_free", "burr_strerror", "burr_last_error", "burr_stage_hash",
+            "burr_stats", "burr_free", "burr_free_many", "burr_strerror", "burr_last_error", "burr_stage_hash",
             "burr_stage_sort", "burr_stage_sort_noalloc", "burr_server_create", "burr_server_submit_build",
             "burr_server_submit_query", "burr_server_wait", "burr_server_handle", "burr_server_release",
             "burr_server_stats", "burr_server_destroy", "burr_set_allocator", "burr_import"]
@@ -108,6 +108,8 @@ def load(path: str | None = None):
         L.burr_stats.restype = i
         L.burr_free.argtypes = [p]
         L.burr_free.restype = None
+        L.burr_free_many.argtypes = [p, u64]
+        L.burr_free_many.restype = None
         L.burr_strerror.argtypes = [i]
         L.burr_strerror.restype = C.c_char_p
         L.burr_last_error.argtypes = []
@@ -197,7 +199,7 @@ class Handle:
     never freed from Python."""
 
     def __init__(self, ptr, r, owned=True):
-        self._h = C.c_void_p(ptr)
+        self._h = ptr or None   # the library's handle pointer (an int), None once freed
         self.r = r
         self.owned = owned
 
@@ -207,9 +209,9 @@ class Handle:
     def free(self):
         if not getattr(self, "owned", False):
             return
-        if getattr(self, "_h", None) is not None and self._h.value:
+        if getattr(self, "_h", None):
             load().burr_free(self._h)
-            self._h = C.c_void_p(None)
+            self._h = None
 
     def query(self, keys, out=None, stream=None):
         """Values of `keys` (torch CUDA/CPU tensor or numpy array), same kind back."""
@@ -273,22 +275,32 @@ def import_export(buf: bytes, stream=None) -> Handle:
     return Handle(out.value, r)
 
 
+def free_all(handles) -> None:
+    """burr_free_many: release many handles (e.g. a batched build's) in one call."""
+    ptrs = [h._h for h in handles if getattr(h, "owned", False) and h._h]
+    if ptrs:
+        load().burr_free_many((C.c_void_p * len(ptrs))(*ptrs), len(ptrs))
+    for h in handles:
+        if getattr(h, "owned", False):
+            h._h = None
+
+
 def build_batch(keys, values, offsets, rs, params: Params | None = None, stream=None, **kw) -> list:
     """burr_build_batch: structure s owns keys[offsets[s]:offsets[s+1]] with r = rs[s].
     Returns one Handle per structure."""
     if params is None:
         params = default_params(**kw)
-    offsets = [int(x) for x in offsets]
-    rs = [int(x) for x in rs]
-    S = len(rs)
-    assert len(offsets) == S + 1
+    offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64).astype(np.uint64))
+    rs_np = np.ascontiguousarray(np.asarray(rs, dtype=np.int64).astype(np.uint32))
+    S = int(rs_np.size)
+    assert offsets.size == S + 1
     kp, st, _kk = _ptr_and_stream(keys, _stream_value(stream))
     vp, _, _vk = _ptr_and_stream(values, st)
-    offs = (C.c_uint64 * (S + 1))(*offsets)
-    rr = (C.c_uint32 * S)(*rs)
+    offs = (C.c_uint64 * (S + 1)).from_buffer_copy(offsets)
+    rr = (C.c_uint32 * S).from_buffer_copy(rs_np)
     outs = (C.c_void_p * S)()
     _check(load().burr_build_batch(kp, vp, offs, rr, S, C.byref(params), st, outs))
-    return [Handle(outs[i], rs[i]) for i in range(S)]
+    return [Handle(p, r) for p, r in zip(outs, rs_np.tolist())]
 
 
 def stage_hash(keys, seed: int, layer_index: int, m: int, stream=None):

@@ -1502,6 +1502,11 @@ void burr_free(burr_handle *h) {
     delete h;
 }
 
+void burr_free_many(burr_handle *const *handles, uint64_t count) {
+    if (!handles) return;
+    for (uint64_t i = 0; i < count; ++i) burr_free(handles[i]);
+}
+
 const char *burr_strerror(int code) {
     switch (code) {
     case BURR_OK: return "ok";
