@@ -128,3 +128,25 @@ def test_batch_cut_search():
     ref = O.build(k_np[a:b], v_np[a:b] & ((1 << rs[big]) - 1), r=rs[big], partition_slots=2048,
                   min_partition_slots=2048, cut_search=O.CUT_MAXPREV)
     assert hs[big].export() == ref.export(), describe_difference(hs[big].export(), ref.export())
+
+
+def test_free_all_releases_a_batch_in_one_call():
+    # burr_free_many: every handle of a batched build released with one call;
+    # the wrappers are marked freed, so neither free() nor a second free_all()
+    # touches them again, and a fresh batch builds the same structures
+    sizes = [5000, 0, 1, 40_000, 12_345]
+    rs = [8, 4, 8, 1, 3]
+    keys, vals, offs = _batch_inputs(sizes, rs)
+    hs = burr.build_batch(keys, vals, offs, rs, partition_slots=4096, min_partition_slots=4096)
+    exports = [h.export() for h in hs]
+    burr.free_all(hs)
+    assert all(h._h is None for h in hs)
+    burr.free_all(hs)
+    for h in hs:
+        h.free()
+    hs2 = burr.build_batch(keys, vals, offs, rs, partition_slots=4096, min_partition_slots=4096)
+    assert [h.export() for h in hs2] == exports
+    burr.free_all(hs2[:2])
+    assert hs2[0]._h is None and hs2[2]._h is not None
+    for h in hs2:
+        h.free()
