@@ -92,6 +92,8 @@ BUILD_CASES = [
     (90_000, 4, dict(partition_slots=128, min_partition_slots=0)),          # a cut at every bucket
     (300_000, 8, dict(lower_partition_slots=0, min_partition_slots=65536)),  # deep layers as layer 0
     (400_000, 8, dict(partition_slots=16384, lower_partition_slots=256, min_partition_slots=256)),
+    (22_736, 8, dict(partition_slots=4096, min_partition_slots=4096)),      # remainder 2048: own partition
+    (22_672, 8, dict(partition_slots=4096, min_partition_slots=4096)),      # remainder 1984: joins the last
 ]
 
 

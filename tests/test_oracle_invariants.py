@@ -168,3 +168,29 @@ def test_lower_layers_cut_at_their_own_partition_size(lower):
         assert L["nparts"] == O.num_partitions(L["m"], Pl, minP)
     if lower and 2 * lower <= s.layer(1)["m"]:
         assert s.layer(1)["nparts"] > O.num_partitions(s.layer(1)["m"], P, minP)
+
+
+@pytest.mark.parametrize("P,minP", [(65536, 4096), (4096, 4096), (1024, 1024), (65536, 0), (2048, 2048)])
+def test_partitions_have_balanced_lengths(P, minP):
+    # Sec. 3 gives each thread a near-equal share.  With cuts at j*P, no
+    # partition may be much longer than P: at most P plus half a partition
+    # (plus 1024 slots for tiny P), and a separate last partition is never
+    # shorter than 1024 slots.  A layer below max(P, minP) is one partition.
+    for m in range(64, 40 * P + 1, 64 * max(1, P // 4096)):
+        K = O.num_partitions(m, P, minP)
+        if m < max(P, minP):
+            assert K == 1
+            continue
+        lens = [P] * (K - 1) + [m - (K - 1) * P]
+        assert all(x > 0 for x in lens)
+        assert max(lens) < P + max(P // 2, 1024)
+        if m % P and K > m // P:
+            assert lens[-1] >= 1024
+
+
+def test_remainder_at_the_threshold_gets_its_own_partition():
+    # the remainder rule at its edge (P = 4096, min 4096: threshold 2048 slots)
+    assert O.num_partitions(5 * 4096 + 2048, 4096, 4096) == 6
+    assert O.num_partitions(5 * 4096 + 1984, 4096, 4096) == 5
+    assert O.num_partitions(1000 * 65536 + 4096, 65536, 4096) == 1001
+    assert O.num_partitions(1000 * 65536 + 4032, 65536, 4096) == 1000
