@@ -11,21 +11,35 @@ namespace {
 
 constexpr int kQThreads = 256;
 
+// Parity of a 64-bit word.
+__device__ __forceinline__ uint32_t parity64q(uint64_t x) {
+    return (uint32_t)__popc((uint32_t)x ^ (uint32_t)(x >> 32)) & 1u;
+}
+
+// Bit k of the value is the parity of c AND the 64 table bits of plane k from
+// slot s on.  Those bits are bits o.. of block word w0 and bits ..o-1 of the
+// next block's word w1 (o = s mod 64), so the parity is that of
+// (w0 & (c << o)) ^ (w1 & (c >> (64 - o))): the row is shifted once per key
+// instead of the window once per plane.
+__device__ __forceinline__ void row_masks(uint64_t c, uint32_t o, uint64_t &cA, uint64_t &cB) {
+    cA = c << o;
+    cB = o ? c >> (64 - o) : 0ull;
+}
+
 // r-bit value of the window [s, s+63] selected by coefficient row c.
 __device__ __forceinline__ uint32_t eval_window(const uint64_t *__restrict__ z, uint32_t r, uint32_t s,
                                                 uint64_t c) {
     const uint64_t blk = s >> 6;
     const uint32_t o = s & 63u;
     const uint64_t *w0 = z + blk * r;
+    uint64_t cA, cB;
+    row_masks(c, o, cA, cB);
     uint32_t v = 0;
     if (o == 0) {
-        for (uint32_t k = 0; k < r; ++k) v |= (uint32_t)(__popcll(__ldg(w0 + k) & c) & 1) << k;
+        for (uint32_t k = 0; k < r; ++k) v |= parity64q(__ldg(w0 + k) & cA) << k;
     } else {
         const uint64_t *w1 = w0 + r;
-        for (uint32_t k = 0; k < r; ++k) {
-            const uint64_t win = (__ldg(w0 + k) >> o) | (__ldg(w1 + k) << (64 - o));
-            v |= (uint32_t)(__popcll(win & c) & 1) << k;
-        }
+        for (uint32_t k = 0; k < r; ++k) v |= parity64q((__ldg(w0 + k) & cA) ^ (__ldg(w1 + k) & cB)) << k;
     }
     return v;
 }
@@ -73,13 +87,11 @@ __device__ __forceinline__ void load_window(const uint64_t *__restrict__ z, uint
 
 template <int R>
 __device__ __forceinline__ uint32_t eval_loaded(const Window<R> &w, uint32_t s, uint64_t c) {
-    const uint32_t o = s & 63u;
+    uint64_t cA, cB;
+    row_masks(c, s & 63u, cA, cB);   // w1 is zero when the window is block-aligned
     uint32_t v = 0;
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const uint64_t win = o ? (w.w0[k] >> o) | (w.w1[k] << (64 - o)) : w.w0[k];
-        v |= (uint32_t)(__popcll(win & c) & 1) << k;
-    }
+    for (int k = 0; k < R; ++k) v |= parity64q((w.w0[k] & cA) ^ (w.w1[k] & cB)) << k;
     return v;
 }
 
