@@ -16,19 +16,23 @@
 //     and, with 2-bit thresholds, the bands [l2,l3), [l1,l2), [l0,l1) are
 //     inserted from the top until one is dependent, which fixes the threshold
 //     exactly as the row-by-row elimination in descending offset order would.
-//     With 1+-bit thresholds (exact threshold t in [0, B]) the least t for
-//     which the rows at offsets >= t insert is found by a search: a set of
-//     rows is independent whenever a superset is, so each probe inserts the
-//     rows of [mid, t_ok) on top of those already kept and either keeps them
-//     (t_ok = mid) or rolls them back (t_fail = mid).
+//   * With 1+-bit thresholds (exact threshold t in [0, B]) t is the least
+//     value for which the rows at offsets >= t insert.  The first pass over
+//     the bucket carries row tags and drops dependent rows instead of
+//     stopping.  The dropped rows' tags span the set's dependencies, and t
+//     follows from them (insert_tagged).  The rows at offsets >= t are then
+//     inserted again as one set.  Where the tags cannot place a dependency,
+//     t is found by probes instead: a set of rows is independent whenever a
+//     superset is, so each probe inserts the rows of [mid, t_ok) on top of
+//     those already kept and either keeps them (t_ok = mid) or rolls them
+//     back (t_fail = mid).
 //   * A set is inserted as a stream: the 32 lanes eliminate one row each and
 //     take their steps in lockstep.  A step is one 128-bit compare-and-swap
 //     on the ring slot of the row's leading bit, which either claims the
 //     slot if it is empty (row and right-hand side stored in one atomic
 //     write) or returns the stored row and right-hand side to XOR with.  Plain
-//     reads of the next few slots (two with 2-bit thresholds, three with
-//     1+-bit ones) are in flight beside the swap, and the elimination goes on
-//     through those that hold stored rows.  This
+//     reads of the next two slots are in flight beside the swap, and the
+//     elimination goes on through those that hold stored rows.  This
 //     is a sequential insertion in claim order: every slot a row eliminated
 //     against was occupied when read and stays so, and a row is stored only
 //     on a slot that was still empty.  Lanes whose row was stored take the
@@ -76,14 +80,14 @@ struct alignas(16) StagedRow {
 
 // Ring slots read ahead of the swap in each step (see stream_insert), per
 // threshold mode: more read-ahead means fewer steps but more instructions per
-// step.  Buckets with 2-bit thresholds are inserted as large sets, where many
-// warps per SM compete for issue slots; the 1+-bit search inserts many small
-// sets, whose time is their number of steps.
+// step, and with many warps per SM competing for issue slots two measured
+// best in both modes (10^8 keys, r=8; 1+-bit: 1, 2, 3, 4 slots gave 27.2,
+// 26.6, 27.5, 27.6 ms per build and query step).
 #ifndef BURR_BAND_LOOKAHEAD_2BIT
 #define BURR_BAND_LOOKAHEAD_2BIT 2
 #endif
 #ifndef BURR_BAND_LOOKAHEAD_1PLUS
-#define BURR_BAND_LOOKAHEAD_1PLUS 3
+#define BURR_BAND_LOOKAHEAD_1PLUS 2
 #endif
 template <bool kExact>
 struct Lookahead {
@@ -93,12 +97,24 @@ struct Lookahead {
 constexpr int kLookMax = Lookahead<false>::value > Lookahead<true>::value ? Lookahead<false>::value
                                                                           : Lookahead<true>::value;
 
+// Tagged sets (1+-bit thresholds): the kTagRows lowest-offset rows of the set
+// carry one bit each in bits 33.. of the right-hand-side word, and a row's tag
+// travels with every XOR, so a row that reduces to zero names the rows of the
+// set that its dependency runs through.
+constexpr uint32_t kTagRows = 31;
+
+__device__ __forceinline__ unsigned long long row_tag(uint32_t k) {
+    return k < kTagRows ? 1ull << (33u + k) : 0ull;
+}
+
 struct BandWarpSmem {
     RingSlot ring[kRing + kLookMax];   // live band window (+ read-ahead pad, never written)
     uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
     StagedRow rows[kStage];        // staged equations, ascending offset
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
     uint32_t ncommit;              // entries of clist
+    uint32_t nfail;                // rows of a tagged set that reduced to zero
+    uint32_t ftag[kTagRows];       // their tags (the first kTagRows of them)
 };
 
 template <typename V>
@@ -196,6 +212,16 @@ __device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, 
     __syncwarp();
 }
 
+// Staging as a call rather than inline code, for the 1+-bit kernel: with the
+// tagged pass beside the probe search, staging inlined at each call site made
+// the kernel take over 240 registers (168 allow six CTAs per SM); as a call it
+// takes 128.  The 2-bit kernel ran equally fast either way and keeps it inline.
+template <typename V>
+__device__ __noinline__ void stage_rows_call(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t base,
+                                             uint32_t cnt, uint32_t bB, int lane) {
+    stage_rows(S, a, x, base, cnt, bB, lane);
+}
+
 // 128-bit compare-and-swap on a ring slot: if the slot is (0, 0) it becomes
 // (c, y); the previous contents are returned either way.
 __device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, unsigned long long y,
@@ -234,7 +260,15 @@ __device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, 
 // step ends at the first leading bit whose slot was not read as occupied,
 // and the next swap goes there.  The row is kept as 64 bits from p plus the
 // kLook bits beyond p+63 that the read-ahead rows bring in.
-template <int kLook>
+//
+// kTag: the rows carry tags (see kTagRows), and a row that reduces to zero does
+// not end the set: its tag is listed in S.ftag (count in S.nfail, from 0), the
+// row is dropped and its lane takes the next one.  This is a sequential
+// insertion in claim order that skips the dependent rows, so each dropped row
+// gives one dependency of the set on the band and the rows stored before it,
+// and together they span all of the set's dependencies.  The result is then
+// kDependent if any row was dropped; a ring overflow still ends the set.
+template <int kLook, bool kTag = false>
 __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
@@ -248,8 +282,11 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         const StagedRow r = S.rows[lo + (uint32_t)lane];
         cur = r.c;
         y = kYValid | r.y;
+        if (kTag) y |= row_tag((uint32_t)lane);
         pos = bB + r.o;
     }
+    uint32_t nf = 0;
+    bool pend = false;   // tagged: the lane's row was dropped; it takes the next one
     int result = kOk;
     for (;;) {
         const uint32_t ri = pos & kRingMask;
@@ -266,15 +303,17 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         const bool stored = has && ((uint32_t)oc & 1u) == 0u;
 
         // Hand-out first: the next row's shared read is in flight during the elimination.
+        const bool take = stored || (kTag && pend);
         const unsigned sm = __ballot_sync(kFull, stored);
+        const unsigned tm = kTag ? __ballot_sync(kFull, take) : sm;
         const uint32_t rank = (uint32_t)__popc(sm & lt);
-        const uint32_t nidx = next + rank;
-        const bool nhas = stored && nidx < hi;
+        const uint32_t nidx = next + (kTag ? (uint32_t)__popc(tm & lt) : rank);
+        const bool nhas = take && nidx < hi;
         StagedRow nr = StagedRow{0ull, 0u, 0u};
         if (nhas) nr = S.rows[nidx];
         if (stored) S.clist[nc + rank] = (uint16_t)ri;
         nc += (uint32_t)__popc(sm);
-        next += (uint32_t)__popc(sm);
+        next += (uint32_t)__popc(tm);
 
         // Elimination for lanes whose swap returned a stored row: against that row, then through
         // the read-ahead slots.  The row is (over : hi32 : lo32), bit j = slot pos + j; bit 0 is
@@ -285,6 +324,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         uint32_t hi32 = (uint32_t)(cur >> 32) ^ (uint32_t)(oc >> 32);
         uint32_t over = 0;
         uint32_t y2 = (uint32_t)y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits
+        uint32_t yh = kTag ? (uint32_t)(y >> 32) ^ (uint32_t)(oy >> 32) : 0u;   // tags (bits 1..)
         bool go = win;
         bool use[kLook > 0 ? kLook : 1];
 #pragma unroll
@@ -303,6 +343,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
             hi32 ^= use[j - 1] ? (uint32_t)(sh >> 32) : 0u;
             over ^= use[j - 1] ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
             y2 ^= use[j - 1] ? (uint32_t)ly[j - 1] : 0u;
+            if (kTag) yh ^= use[j - 1] ? (uint32_t)(ly[j - 1] >> 32) : 0u;
         }
         // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0; it is
         // almost always in the low word
@@ -326,26 +367,47 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         const bool ovf = act && !zero && npos - bB >= (uint32_t)kRing;
         if (act) {
             cur = ((unsigned long long)n1 << 32) | n0;
-            y = kYValid | y2;
+            y = kTag ? ((unsigned long long)(yh | 1u) << 32) | y2 : kYValid | y2;
             pos = npos;
         }
-        if (stored) {
+        if (take) {
             has = nhas;
             cur = nr.c;
             y = nhas ? kYValid | nr.y : 0ull;
+            if (kTag && nhas) y |= row_tag(nidx - lo);
             if (nhas) pos = bB + nr.o;
+            pend = false;
         }
         const unsigned bm = __ballot_sync(kFull, dep || ovf);
-        const unsigned hm = __ballot_sync(kFull, has);
+        unsigned hm = __ballot_sync(kFull, has);
         if (bm) {
-            result = __ballot_sync(kFull, ovf) ? kOverflow : kDependent;
-            break;
+            const unsigned om = __ballot_sync(kFull, ovf);
+            if (!kTag || om) {
+                result = om ? kOverflow : kDependent;
+                break;
+            }
+            // tagged: list the dropped rows' tags; their lanes swap (0, 0) once and then take the
+            // next rows
+            const uint32_t dr = (uint32_t)__popc(bm & lt);
+            if (dep) {
+                if (nf + dr < kTagRows) S.ftag[nf + dr] = yh >> 1;
+                has = false;
+                cur = 0;
+                y = 0;
+                pend = true;
+            }
+            nf += (uint32_t)__popc(bm);
+            hm = __ballot_sync(kFull, has || (pend && next < hi));
         }
         if (!hm) break;
     }
     __syncwarp();
-    if (lane == 0) S.ncommit = nc;
+    if (lane == 0) {
+        S.ncommit = nc;
+        if (kTag) S.nfail = nf;
+    }
     __syncwarp();
+    if (kTag && result == kOk && nf) result = kDependent;
     return result;
 }
 
@@ -359,7 +421,8 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
     for (uint32_t base = rs; base < re; base += kStage) {
         const uint32_t cnt = min((uint32_t)kStage, re - base);
         if (staged_base != base) {
-            stage_rows(S, a, x, base, cnt, bB, lane);
+            if (kExact) stage_rows_call(S, a, x, base, cnt, bB, lane);
+            else stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
         const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, lane);
@@ -372,13 +435,69 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
     return kOk;
 }
 
+constexpr uint32_t kTagUnknown = 0xffffffffu;
+
+// 1+-bit threshold of a bucket whose rows fit one stage, from one tagged pass
+// over its rows at offsets >= forced.  The set's dependencies form a space D
+// spanned by the dropped rows' dependency vectors (one per dropped row).  The
+// rows at offsets >= t insert iff no nonzero vector of D lies inside them, so
+// the least such t is one above the largest, over D, of the lowest offset a
+// vector contains.  Row i of the set (ascending offset) is tag bit i for
+// i < kTagRows, every later row sits at an offset at least as high, and a tag
+// is the vector's restriction to the tagged rows: after a reduction of the
+// tags to distinct lowest bits, the largest lowest bit b gives t = offset of
+// row b + 1.  A tag that reduces to zero means a dependency among untagged
+// rows only, which the tags cannot place: kTagUnknown.
+// Returns forced if the set inserts (its rows stay in the band), else t with
+// nothing of the set left in the band, kTagUnknown (same), or B + 1 on a ring
+// overflow.
+template <typename V>
+__device__ uint32_t insert_tagged(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
+                                  uint32_t bB, uint32_t forced, uint32_t &staged, int lane) {
+    if (staged != rs) {
+        stage_rows_call(S, a, x, rs, re - rs, bB, lane);
+        staged = rs;
+    }
+    if (lane == 0) S.ncommit = 0;
+    __syncwarp();
+    const uint32_t lo = S.first[forced];
+    const int rc = stream_insert<Lookahead<true>::value, true>(S, lo, S.first[x.L.B], bB, lane);
+    const uint32_t nc = S.ncommit;
+    if (rc == kOk) {
+        for (uint32_t i = lane; i < nc; i += 32) S.ring[S.clist[i]].y &= kYValid | 0xffffffffull;   // drop the tags
+        __syncwarp();
+        return forced;
+    }
+    rollback(S, nc, lane);
+    if (rc == kOverflow) {
+        if (lane == 0) atomicOr(a.err, kErrRingOverflow);
+        return x.L.B + 1u;
+    }
+    const uint32_t nf = S.nfail;
+    if (nf > kTagRows) return kTagUnknown;
+    uint32_t v = (uint32_t)lane < nf ? S.ftag[lane] : 0u;
+    bool piv = false;
+    int top = -1;
+    for (int b = 0; b < (int)kTagRows; ++b) {
+        const unsigned cand = __ballot_sync(kFull, !piv && ((v >> b) & 1u));
+        if (!cand) continue;
+        const int p = __ffs((int)cand) - 1;
+        const uint32_t pv = __shfl_sync(kFull, v, p);
+        if (lane == p) piv = true;
+        else if ((cand >> lane) & 1u) v ^= pv;
+        top = b;
+    }
+    if (__ballot_sync(kFull, (uint32_t)lane < nf && !piv) || top < 0) return kTagUnknown;
+    return S.rows[lo + (uint32_t)top].o + 1u;
+}
+
 // Offsets above the failing threshold tried first (8, 12, 16 and 24 measured;
-// 8 and 16 tie at 10^8 keys).
+// 8 and 16 tied at 10^8 keys when every failing bucket was searched by probes).
 constexpr uint32_t kFirstProbe = 16;
 
-// 1+-bit threshold of a bucket whose rows at offsets >= forced are dependent:
-// the least t for which the rows at offsets >= t insert, those rows left
-// inserted.  Rows at offsets >= t_fail are dependent, those >= t_ok are kept;
+// 1+-bit threshold of a bucket whose rows at offsets >= forced are dependent,
+// by probes (where the tagged pass cannot decide it): the least t for which
+// the rows at offsets >= t insert, those rows left inserted.  Rows at offsets >= t_fail are dependent, those >= t_ok are kept;
 // exact thresholds are mostly small (a few rows at the lowest offsets), so the
 // first probe keeps all but the lowest 16 offsets and bisection follows.
 // Returns B + 1 on a ring overflow.
@@ -525,16 +644,26 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         uint32_t texact = forced;
         if (re > rs) {
             uint32_t staged = 0xffffffffu;
-            int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
-            if (rc == kOverflow) return;
-            if (rc == kDependent) {
+            bool search = false;   // 1+-bit: find the threshold by probes
+            if (kExact && !L.fallback && re - rs <= (uint32_t)kStage) {
+                // one tagged pass gives the threshold; the search only where the tags do not decide
+                texact = insert_tagged(S, a, x, rs, re, (uint32_t)bB, forced, staged, lane);
+                if (texact == L.B + 1u) return;   // ring overflow (recorded)
+                if (texact != kTagUnknown && texact > forced) {
+                    const int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, texact, L.B, staged, lane);
+                    if (rc == kOverflow) return;
+                    if (rc != kOk) texact = kTagUnknown;   // not expected: the rows at offsets >= t are independent
+                }
+                search = texact == kTagUnknown;
+            } else if (const int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
+                       rc != kOk) {
+                if (rc == kOverflow) return;
                 if (L.fallback) {
                     if (lane == 0) atomicOr(x.fail ? x.fail : a.err, kErrUnsolvable);
                     return;
                 }
                 if (kExact) {
-                    texact = exact_threshold(S, a, x, rs, re, (uint32_t)bB, forced, staged, lane);
-                    if (texact > L.B) return;   // ring overflow (recorded)
+                    search = true;
                 } else {
                     code = 3;
                     for (int k = 2; k >= 0; --k) {
@@ -555,6 +684,10 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                         code = (uint32_t)k;
                     }
                 }
+            }
+            if (kExact && search) {
+                texact = exact_threshold(S, a, x, rs, re, (uint32_t)bB, forced, staged, lane);
+                if (texact > L.B) return;   // ring overflow (recorded)
             }
             const uint32_t t = kExact ? texact : lv[code];
             if (!L.fallback && t > 0) emit_bumped(a, x, rs, re, (uint32_t)bB, t, lane);
