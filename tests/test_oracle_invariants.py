@@ -149,6 +149,77 @@ def test_1plus_permutation_invariance():
     assert O.build(k[perm], v[perm], **kw).export() == a
 
 
+def _insert_tagged(band, s, c, tag):
+    """Ribbon insertion of row c at slot s into band {slot: (row, tag)}; tags are XORed along.
+    Returns the slot stored at, or None and the accumulated tag when the row reduces to zero."""
+    pos, cur = s, c
+    while pos in band:
+        bc, bt = band[pos]
+        cur ^= bc
+        tag ^= bt
+        if cur == 0:
+            return None, tag
+        tz = (cur & -cur).bit_length() - 1
+        pos += tz
+        cur >>= tz
+    band[pos] = (cur, tag)
+    return pos, None
+
+
+@pytest.mark.parametrize("alpha", [1.015, 1.0])
+def test_1plus_threshold_follows_from_dependencies_in_any_order(alpha):
+    # Sec. 2, 1+-bit thresholds: a bucket's threshold is the least t whose rows at offsets >= t
+    # insert.  The set's dependencies do not depend on the insertion order, so t can be
+    # recovered from one insertion of the whole bucket in any order: tag the rows of the
+    # bucket (ascending offset), drop the rows that reduce to zero, reduce their tags to
+    # distinct lowest bits; t = offset of the row of the largest such bit + 1.  Checked against
+    # the oracle's descending-offset insertion on hashed equations, bucket by bucket.
+    n, r, B = 24_000, 8, 128
+    k, v = _kv(n, r, seed=4242)
+    m = O.layer_slots(n, alpha)
+    sigma = O.layer_seed(7, 0)
+    res = O.build_layer(k, v, r, m, sigma, mode=O.THRESH_1PLUS)
+    assert res.status == 0
+    starts, coeffs = O.hash_many(k, sigma, m)
+    buckets = {}
+    for s, c in zip(starts.tolist(), coeffs.tolist()):
+        buckets.setdefault(s // B, []).append((s, c))
+    rng = np.random.default_rng(11)
+    band, failing = {}, 0
+    for b in range(len(res.texact)):
+        rows = sorted(buckets.get(b, []), key=lambda sc: sc[0] % B)
+        order = rng.permutation(len(rows))
+        stored, tags = [], []
+        for i in order:
+            s, c = rows[i]
+            p, tag = _insert_tagged(band, s, c, 1 << int(i))
+            (stored.append(p) if p is not None else tags.append(tag))
+        t = 0
+        if not tags:
+            for p in stored:                             # the bucket inserted: clear its tags
+                band[p] = (band[p][0], 0)
+        else:
+            failing += 1
+            for p in stored:
+                del band[p]
+            top = -1
+            for bit in range(len(rows)):
+                piv = next((j for j, x in enumerate(tags) if (x >> bit) & 1 and x & ((1 << bit) - 1) == 0), None)
+                if piv is None:
+                    continue
+                for j in range(len(tags)):
+                    if j != piv and (tags[j] >> bit) & 1:
+                        tags[j] ^= tags[piv]
+                top = bit
+            assert all(x != 0 for x in tags)          # independent dependencies, one per dropped row
+            t = rows[top][0] % B + 1
+            for s, c in rows:                            # the rows above t insert, untagged
+                if s % B >= t:
+                    assert _insert_tagged(band, s, c, 0)[0] is not None
+        assert t == int(res.texact[b]), b
+    assert failing >= 20
+
+
 def test_invalid_threshold_mode_rejected():
     k, v = _kv(10, 8)
     assert O.build(k, v, threshold_mode=2).status == O.EINVAL
