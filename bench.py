@@ -78,10 +78,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(kernel_src: str):
-    """Per-launch DRAM bytes of the layer-0 band launch from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_band_1e8_r8_traffic.txt")
+def ncu_band_summary(kernel_src: str, path: str | None = None):
+    """Per-launch DRAM bytes and warp instructions of the 10^8-key layer-0 band
+    launch (2-bit thresholds, 1-byte values) from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = path or os.path.join(ROOT, "profiles", "k_band_1e8_r8_traffic.txt")
     try:
         kv = {}
         for line in open(path):
@@ -91,9 +92,21 @@ def ncu_traffic(kernel_src: str):
         src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         if kv.get("kernel_source_sha256_16") != src_hash:
             return None
-        return float(kv["dram_bytes_per_launch_scaled"])
+        inst = kv.get("warp_instructions_per_launch_scaled")
+        return {"dram_bytes": float(kv["dram_bytes_per_launch_scaled"]),
+                "warp_instructions": float(inst) if inst else None}
     except Exception:
         return None
+
+
+def issue_roofline(warp_instructions, band_ms, sms, sm_max_mhz):
+    """Warp instructions per second of the band launch against the issue peak:
+    four schedulers per SM, one warp instruction each per cycle, at the SM clock."""
+    peak = sms * 4 * sm_max_mhz * 1e6
+    achieved = warp_instructions / (band_ms / 1e3)
+    return {"warp_instructions": warp_instructions, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "peak_derivation": f"{sms} SMs x 4 schedulers x 1 warp instruction/cycle x {sm_max_mhz:.0f} MHz"}
 
 
 class ClockSampler:
@@ -576,7 +589,11 @@ def main():
     band_bytes = n0 * (8 + vb) + (nb0 + 1) * 4 + m0 * (8 + vb) + bump0 * (8 + vb) + ((nb0 + 31) // 32) * 8
     peak, peak_kind = measured_peaks()
     achieved = band_bytes / (band0 / 1e3) / 1e9
-    traffic = ncu_traffic(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
+    # the ncu figures belong to the captured instantiation: 2-bit thresholds, 1-byte values
+    summ = (ncu_band_summary(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
+            if tmode(a) == 0 and vb == 1 else None)
+    scale = n0 / 1e8                       # the summary is scaled to a 10^8-key launch
+    traffic = summ["dram_bytes"] * scale if summ else None
     # space overhead: bits of the device tables (Z, thresholds) over r*n
     overhead = (st0["table_bytes"] - 64) * 8 / (r * n) - 1
     # whole-stage rooflines against compulsory bytes:
@@ -621,6 +638,11 @@ def main():
         "gpu_launches": launches[0],
     }
     line["clocks"] = clk.summary()
+    if summ and summ["warp_instructions"]:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = line["clocks"].get("sm_max_mhz") or 2070.0
+        line["roofline"]["issue"] = issue_roofline(summ["warp_instructions"] * scale, band0, sms, mhz)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     if not a.no_e2e:
