@@ -497,10 +497,11 @@ constexpr uint32_t kFirstProbe = 16;
 
 // 1+-bit threshold of a bucket whose rows at offsets >= forced are dependent,
 // by probes (where the tagged pass cannot decide it): the least t for which
-// the rows at offsets >= t insert, those rows left inserted.  Rows at offsets >= t_fail are dependent, those >= t_ok are kept;
-// exact thresholds are mostly small (a few rows at the lowest offsets), so the
-// first probe keeps all but the lowest 16 offsets and bisection follows.
-// Returns B + 1 on a ring overflow.
+// the rows at offsets >= t insert, those rows left inserted.  Rows at offsets
+// >= t_fail are dependent, those >= t_ok are kept; exact thresholds are mostly
+// small (a few rows at the lowest offsets), so the first probe keeps all but
+// the lowest 16 offsets and bisection follows.  Returns B + 1 on a ring
+// overflow.
 template <typename V>
 __device__ __forceinline__ uint32_t exact_threshold(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs,
                                                  uint32_t re, uint32_t bB, uint32_t forced, uint32_t &staged,
