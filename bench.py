@@ -50,7 +50,8 @@ def args_():
     ap.add_argument("--thresholds", default="2bit", choices=["2bit", "1plus"],
                     help="threshold storage: 2-bit levels or 1+-bit (bit per bucket + exact thresholds)")
     ap.add_argument("--min-partition-slots", type=int, default=4096)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 22, help="keys of the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24,
+                    help="keys of the oracle sample (about 12 s of serial CPU work)")
     ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
