@@ -159,9 +159,13 @@ __device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int 
 
 // Stage rows [base, base+cnt) (cnt <= kStage) of the bucket starting at slot
 // bB: equations in ascending offset order; S.first[o] = first index with
-// offset >= o.
+// offset >= o.  A call, not inline code: inlined at its call sites, staging
+// kept registers live across the elimination loops (166 registers in the 2-bit
+// kernel, over 240 in the 1+-bit one); as a call both take 128, so 8 CTAs of 2
+// warps fit per SM instead of 6.  Measured: equal at 10^8 keys (all partitions
+// resident either way), layer-0 band 76.9 -> 68.2 ms at 10^9 keys.
 template <typename V>
-__device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t base, uint32_t cnt,
+__device__ __noinline__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t base, uint32_t cnt,
                            uint32_t bB, int lane) {
     const LayerDesc &L = x.L;
     for (int i = lane; i < 132; i += 32) S.first[i] = 0;
@@ -210,16 +214,6 @@ __device__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, 
         }
     }
     __syncwarp();
-}
-
-// Staging as a call rather than inline code, for the 1+-bit kernel: with the
-// tagged pass beside the probe search, staging inlined at each call site made
-// the kernel take over 240 registers (168 allow six CTAs per SM); as a call it
-// takes 128.  The 2-bit kernel ran equally fast either way and keeps it inline.
-template <typename V>
-__device__ __noinline__ void stage_rows_call(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t base,
-                                             uint32_t cnt, uint32_t bB, int lane) {
-    stage_rows(S, a, x, base, cnt, bB, lane);
 }
 
 // 128-bit compare-and-swap on a ring slot: if the slot is (0, 0) it becomes
@@ -421,8 +415,7 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
     for (uint32_t base = rs; base < re; base += kStage) {
         const uint32_t cnt = min((uint32_t)kStage, re - base);
         if (staged_base != base) {
-            if (kExact) stage_rows_call(S, a, x, base, cnt, bB, lane);
-            else stage_rows(S, a, x, base, cnt, bB, lane);
+            stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
         const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, lane);
@@ -455,7 +448,7 @@ template <typename V>
 __device__ uint32_t insert_tagged(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
                                   uint32_t bB, uint32_t forced, uint32_t &staged, int lane) {
     if (staged != rs) {
-        stage_rows_call(S, a, x, rs, re - rs, bB, lane);
+        stage_rows(S, a, x, rs, re - rs, bB, lane);
         staged = rs;
     }
     if (lane == 0) S.ncommit = 0;
@@ -564,11 +557,12 @@ __device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, con
 // kExact: 1+-bit thresholds (exact per bucket) instead of 2-bit codes; a
 // template parameter so that each mode gets its own register allocation.
 template <typename V, bool kExact>
-// The kernel needs at most 170 registers for six CTAs of two warps per SM, so
-// that all 1504 layer-0 partitions of 10^8 keys are resident at once (the
-// compiler's own choice is 166).  Measured: at 186 registers (5 CTAs per SM)
-// the layer-0 band took 15.5 ms instead of 9.7; capped at 128 registers (8
-// CTAs, with spills) 13.4 ms; capped at 168 registers 9.9 ms.
+// All 1504 layer-0 partitions of 10^8 keys are resident at once when the
+// kernel takes at most 170 registers (six CTAs of two warps per SM).  Measured
+// with staging inline: at 186 registers (5 CTAs per SM) the layer-0 band took
+// 15.5 ms instead of 9.7; with a 128-register cap (spills inside the
+// elimination loop) 13.4 ms.  With staging as a call it takes 128 without
+// such spills (see stage_rows).
 __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
