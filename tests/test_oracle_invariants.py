@@ -166,19 +166,22 @@ def _insert_tagged(band, s, c, tag):
     return pos, None
 
 
-@pytest.mark.parametrize("alpha", [1.015, 1.0])
-def test_1plus_threshold_follows_from_dependencies_in_any_order(alpha):
+@pytest.mark.parametrize("alpha,cut_every", [(1.015, 0), (1.0, 0), (1.015, 2048)])
+def test_1plus_threshold_follows_from_dependencies_in_any_order(alpha, cut_every):
     # Sec. 2, 1+-bit thresholds: a bucket's threshold is the least t whose rows at offsets >= t
     # insert.  The set's dependencies do not depend on the insertion order, so t can be
     # recovered from one insertion of the whole bucket in any order: tag the rows of the
     # bucket (ascending offset), drop the rows that reduce to zero, reduce their tags to
     # distinct lowest bits; t = offset of the row of the largest such bit + 1.  Checked against
-    # the oracle's descending-offset insertion on hashed equations, bucket by bucket.
-    n, r, B = 24_000, 8, 128
+    # the oracle's descending-offset insertion on hashed equations, bucket by bucket.  With cuts
+    # (Sec. 3), the first bucket of a partition starts from the forced threshold w: its set is
+    # the rows at offsets >= w, and t >= w.
+    n, r, B, w = 24_000, 8, 128, 64
     k, v = _kv(n, r, seed=4242)
     m = O.layer_slots(n, alpha)
     sigma = O.layer_seed(7, 0)
-    res = O.build_layer(k, v, r, m, sigma, mode=O.THRESH_1PLUS)
+    cuts = list(range(cut_every, m - w, cut_every)) if cut_every else []
+    res = O.build_layer(k, v, r, m, sigma, cuts=cuts, mode=O.THRESH_1PLUS)
     assert res.status == 0
     starts, coeffs = O.hash_many(k, sigma, m)
     buckets = {}
@@ -186,15 +189,17 @@ def test_1plus_threshold_follows_from_dependencies_in_any_order(alpha):
         buckets.setdefault(s // B, []).append((s, c))
     rng = np.random.default_rng(11)
     band, failing = {}, 0
+    forced_buckets = {c // B for c in cuts}
     for b in range(len(res.texact)):
-        rows = sorted(buckets.get(b, []), key=lambda sc: sc[0] % B)
+        forced = w if b in forced_buckets else 0
+        rows = [sc for sc in sorted(buckets.get(b, []), key=lambda sc: sc[0] % B) if sc[0] % B >= forced]
         order = rng.permutation(len(rows))
         stored, tags = [], []
         for i in order:
             s, c = rows[i]
             p, tag = _insert_tagged(band, s, c, 1 << int(i))
             (stored.append(p) if p is not None else tags.append(tag))
-        t = 0
+        t = forced
         if not tags:
             for p in stored:                             # the bucket inserted: clear its tags
                 band[p] = (band[p][0], 0)
