@@ -36,6 +36,9 @@
  * code (known-answer vectors of SplitMix64, an inverse of the mixer, a dense
  * GF(2) brute-force solver, the query invariant, permutation invariance).
  */
+#define _POSIX_C_SOURCE 200809L
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -210,6 +213,336 @@ int or_forced_code(const uint32_t levels[4], uint32_t w)
 }
 
 /*
+ * What the steps of one layer build share.  rows: the layer's equations, in
+ * bucket order after step 2; C/Y: the band (C[p] = stored coefficient row,
+ * bit 0 = pivot p, 0 = empty slot; Y[p] = its right-hand side); slot_of[k]:
+ * slot of row k while it is stored, -1 otherwise; code_of / texact: the
+ * threshold of every bucket (2-bit code / exact threshold); Zs: the solution,
+ * one r-bit value per slot.
+ */
+typedef struct {
+    or_row *rows;
+    uint64_t n, m, nb;
+    uint32_t r, B, w, mode;
+    int fallback, forced;
+    uint32_t t_forced;
+    const uint32_t *levels;
+    const uint64_t *cuts;
+    uint64_t ncuts;
+    uint64_t *C;
+    uint32_t *Y;
+    int64_t *slot_of;
+    uint8_t *code_of;
+    uint8_t *texact;
+    uint32_t *Zs;
+} or_work;
+
+/*
+ * Step 3 for rows [i0, i1), which hold whole buckets: insertion bucket by
+ * bucket; on the first failure the bucket's threshold is set and every row of
+ * the bucket below it is rolled back.  Bumped rows are appended to
+ * bumped_keys/vals (count in *nbumped).  Returns 0, or OR_FAIL when a row of
+ * the base case does not insert.
+ */
+static int or_insert_rows(or_work *W, uint64_t i0, uint64_t i1,
+                          uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                          or_stats *st)
+{
+    const or_row *rows = W->rows;
+    const uint64_t *cuts = W->cuts;
+    const uint64_t ncuts = W->ncuts;
+    const uint32_t B = W->B, mode = W->mode;
+    const uint32_t *levels = W->levels;
+    const int fallback = W->fallback, forced = W->forced;
+    uint64_t *C = W->C;
+    uint32_t *Y = W->Y;
+    int64_t *slot_of = W->slot_of;
+    uint8_t *texact = W->texact;
+    uint64_t i = i0, cut_idx = 0;
+    int status = 0;
+    while (i < i1) {
+        uint64_t b = rows[i].start / B;
+        uint64_t j = i;
+        while (j < i1 && rows[j].start / B == b) j++;
+        /* rows[i..j) is bucket b in descending offset order */
+        while (cut_idx < ncuts && cuts[cut_idx] < b * B) cut_idx++;
+        int after_cut = (cut_idx < ncuts && cuts[cut_idx] == b * B);
+        uint32_t t = (after_cut && !fallback) ? W->t_forced : 0;
+        uint32_t code = (after_cut && !fallback && mode == OR_THRESH_2BIT) ? (uint32_t)forced : 0;
+        for (uint64_t k = i; k < j; k++) slot_of[k] = -1;
+        for (uint64_t k = i; k < j; k++) {
+            uint32_t off = (uint32_t)(rows[k].start % B);
+            if (off < t) break;              /* forced bump below the level */
+            int64_t p = or_insert(C, Y, rows[k].start, rows[k].coeff, rows[k].val,
+                                  st ? &st->xor_steps : &(uint64_t){0});
+            if (st) st->inserted++;
+            if (p >= 0) {
+                slot_of[k] = p;
+                if (st && (uint64_t)p - rows[k].start > st->max_drift)
+                    st->max_drift = (uint64_t)p - rows[k].start;
+                continue;
+            }
+            if (fallback) { status = OR_FAIL; break; }
+            if (mode == OR_THRESH_1PLUS) {
+                t = off + 1;                 /* rows at offsets >= t were all kept */
+            } else {
+                code = or_level_above(levels, off);
+                if (after_cut && code < (uint32_t)forced) code = (uint32_t)forced;
+                t = levels[code];
+            }
+            /* roll back every row of this bucket below the new threshold */
+            for (uint64_t q = i; q < k; q++) {
+                uint32_t oq = (uint32_t)(rows[q].start % B);
+                if (oq < t && slot_of[q] >= 0) {
+                    C[slot_of[q]] = 0;
+                    Y[slot_of[q]] = 0;
+                    slot_of[q] = -1;
+                }
+            }
+            break;
+        }
+        if (status) break;
+        if (!fallback) {
+            if (mode == OR_THRESH_1PLUS)
+                texact[b] = (uint8_t)t;
+            else
+                W->code_of[b] = (uint8_t)code;
+            for (uint64_t k = i; k < j; k++) {
+                if ((uint32_t)(rows[k].start % B) < t) {
+                    bumped_keys[*nbumped] = rows[k].key;
+                    bumped_vals[*nbumped] = rows[k].val;
+                    (*nbumped)++;
+                }
+            }
+        }
+        i = j;
+    }
+    return status;
+}
+
+/* Step 4 for slots [s0, s1): back-substitution, right to left, free slots
+ * fixed to 0 (READING: the paper is silent on free variables). */
+static void or_backsub_slots(or_work *W, uint64_t s0, uint64_t s1)
+{
+    const uint64_t *C = W->C;
+    const uint32_t *Y = W->Y;
+    uint32_t *Zs = W->Zs;
+    for (uint64_t s = s1; s-- > s0;) {
+        if (C[s] == 0) { Zs[s] = 0; continue; }
+        uint32_t v = Y[s];
+        for (int k = 1; k < 64; k++)
+            if ((C[s] >> k) & 1ULL) v ^= Zs[s + (uint64_t)k];
+        Zs[s] = v;
+    }
+}
+
+/* The solution of slots [s0, s1) (multiples of 64) as interleaved bit planes:
+ * bit k of slot s is bit s%64 of z[(s/64)*r + k]. */
+static void or_pack_planes(const or_work *W, uint64_t s0, uint64_t s1, uint64_t *z)
+{
+    const uint32_t r = W->r;
+    memset(z + (s0 / 64) * r, 0, sizeof(uint64_t) * ((s1 - s0) / 64) * r);
+    for (uint64_t s = s0; s < s1; s++)
+        for (uint32_t k = 0; k < r; k++)
+            if ((W->Zs[s] >> k) & 1u)
+                z[(s / 64) * r + k] |= 1ULL << (s % 64);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same steps with the partitions spread over host threads (the paper's  */
+/* parallel construction, Sec. 3: once the cuts are placed, every partition  */
+/* is inserted and back-substituted on its own).                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct or_mt or_mt;
+typedef void (*or_task)(or_mt *M, unsigned tid);
+
+struct or_mt {
+    or_work *W;
+    const uint64_t *keys;
+    const uint32_t *vals;
+    uint32_t mask;
+    uint64_t sigma;
+    unsigned nthreads;
+    uint64_t K;                 /* partitions: K = ncuts + 1 */
+    uint32_t *part_of_bucket;   /* bucket -> partition */
+    or_row *hashed;             /* step 1 output, input order */
+    uint64_t *cnt;              /* [tid][K]: rows of the thread's input chunk per partition */
+    uint64_t *prow;             /* [K+1]: first row of each partition after step 2 */
+    uint64_t *pbumped;          /* [K]: bumped rows of each partition (at bumped + prow[q]) */
+    uint64_t *bumped_keys;
+    uint32_t *bumped_vals;
+    uint64_t *z;
+    or_stats *tstats;           /* [tid] */
+    int *tstatus;               /* [tid] */
+    atomic_uint_fast64_t next;  /* next partition to take */
+    or_task task;
+};
+
+typedef struct { or_mt *M; unsigned tid; } or_thread_arg;
+
+static void *or_thread_main(void *p)
+{
+    or_thread_arg *a = (or_thread_arg *)p;
+    a->M->task(a->M, a->tid);
+    return NULL;
+}
+
+/* Run M->task on every thread id and wait for all of them (thread 0 runs on
+ * the calling thread). */
+static int or_run(or_mt *M, or_task task)
+{
+    pthread_t th[OR_MAX_THREADS];
+    or_thread_arg arg[OR_MAX_THREADS];
+    unsigned started = 1;
+    M->task = task;
+    atomic_store(&M->next, 0);
+    for (unsigned t = 1; t < M->nthreads; t++) {
+        arg[t].M = M;
+        arg[t].tid = t;
+        if (pthread_create(&th[t], NULL, or_thread_main, &arg[t]) != 0) break;
+        started++;
+    }
+    task(M, 0);
+    for (unsigned t = 1; t < started; t++) pthread_join(th[t], NULL);
+    /* partitions left behind by threads that could not start */
+    if (started < M->nthreads)
+        for (unsigned t = started; t < M->nthreads; t++) task(M, t);
+    return 0;
+}
+
+static void or_chunk(const or_mt *M, unsigned tid, uint64_t *lo, uint64_t *hi)
+{
+    uint64_t n = M->W->n, per = (n + M->nthreads - 1) / M->nthreads;
+    *lo = per * tid < n ? per * tid : n;
+    *hi = per * (tid + 1) < n ? per * (tid + 1) : n;
+}
+
+/* Step 1 on the thread's chunk of keys, counting rows per partition. */
+static void or_task_hash(or_mt *M, unsigned tid)
+{
+    or_work *W = M->W;
+    uint64_t lo, hi, *cnt = M->cnt + (uint64_t)tid * M->K;
+    or_chunk(M, tid, &lo, &hi);
+    for (uint64_t i = lo; i < hi; i++) {
+        or_row *row = &M->hashed[i];
+        row->key = M->keys[i];
+        row->val = M->vals[i] & M->mask;
+        or_hash(M->keys[i], M->sigma, W->m, W->w, &row->start, &row->coeff);
+        cnt[M->part_of_bucket[row->start / W->B]]++;
+    }
+}
+
+/* Step 2, first half: the rows of the thread's chunk to their partitions. */
+static void or_task_scatter(or_mt *M, unsigned tid)
+{
+    uint64_t lo, hi, *pos = M->cnt + (uint64_t)tid * M->K;
+    or_chunk(M, tid, &lo, &hi);
+    for (uint64_t i = lo; i < hi; i++) {
+        const or_row *row = &M->hashed[i];
+        M->W->rows[pos[M->part_of_bucket[row->start / M->W->B]]++] = *row;
+    }
+}
+
+/* Step 2, second half, then steps 3 and 4, one partition at a time. */
+static void or_task_sort(or_mt *M, unsigned tid)
+{
+    (void)tid;
+    for (uint64_t q; (q = atomic_fetch_add(&M->next, 1)) < M->K;)
+        qsort(M->W->rows + M->prow[q], M->prow[q + 1] - M->prow[q], sizeof(or_row), or_row_cmp);
+}
+
+static void or_task_insert(or_mt *M, unsigned tid)
+{
+    for (uint64_t q; (q = atomic_fetch_add(&M->next, 1)) < M->K;) {
+        uint64_t nb = 0;
+        int rc = or_insert_rows(M->W, M->prow[q], M->prow[q + 1], M->bumped_keys + M->prow[q],
+                                M->bumped_vals + M->prow[q], &nb, &M->tstats[tid]);
+        M->pbumped[q] = nb;
+        if (rc) M->tstatus[tid] = rc;
+    }
+}
+
+static void or_task_backsub(or_mt *M, unsigned tid)
+{
+    (void)tid;
+    const or_work *W = M->W;
+    for (uint64_t q; (q = atomic_fetch_add(&M->next, 1)) < M->K;) {
+        /* partition q owns [cut_{q} + w, cut_{q+1} + w): its kept rows start
+         * at or after the forced level of its first bucket (>= w) and before
+         * the next cut, so their supports stay inside */
+        uint64_t s0 = q == 0 ? 0 : W->cuts[q - 1] + W->w;
+        uint64_t s1 = q + 1 == M->K ? W->m : W->cuts[q] + W->w;
+        if (s1 <= s0) continue;
+        or_backsub_slots(M->W, s0, s1);
+        or_pack_planes(W, s0, s1, M->z);
+    }
+}
+
+/* Steps 1-4 of a layer with nthreads threads (W set up, rows allocated). */
+static int or_layer_steps_mt(or_work *W, const uint64_t *keys, const uint32_t *vals, uint32_t mask,
+                             uint64_t sigma, unsigned nthreads, uint64_t *z,
+                             uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                             or_stats *st)
+{
+    or_mt M;
+    memset(&M, 0, sizeof(M));
+    M.W = W; M.keys = keys; M.vals = vals; M.mask = mask; M.sigma = sigma;
+    M.nthreads = nthreads; M.K = W->ncuts + 1; M.z = z;
+    M.bumped_keys = bumped_keys; M.bumped_vals = bumped_vals;
+    M.part_of_bucket = (uint32_t *)malloc(sizeof(uint32_t) * (W->nb ? W->nb : 1));
+    M.hashed = (or_row *)malloc(sizeof(or_row) * W->n);
+    M.cnt = (uint64_t *)calloc((uint64_t)nthreads * M.K, sizeof(uint64_t));
+    M.prow = (uint64_t *)calloc(M.K + 1, sizeof(uint64_t));
+    M.pbumped = (uint64_t *)calloc(M.K, sizeof(uint64_t));
+    M.tstats = (or_stats *)calloc(nthreads, sizeof(or_stats));
+    M.tstatus = (int *)calloc(nthreads, sizeof(int));
+    int status = 0;
+    if (!M.part_of_bucket || !M.hashed || !M.cnt || !M.prow || !M.pbumped || !M.tstats || !M.tstatus)
+        status = OR_ENOMEM;
+    if (status == 0) {
+        for (uint64_t b = 0, q = 0; b < W->nb; b++) {
+            while (q < W->ncuts && W->cuts[q] <= b * W->B) q++;
+            M.part_of_bucket[b] = (uint32_t)q;
+        }
+        or_run(&M, or_task_hash);
+        /* write offsets: partition q's rows of thread t follow those of threads < t */
+        uint64_t pos = 0;
+        for (uint64_t q = 0; q < M.K; q++) {
+            M.prow[q] = pos;
+            for (unsigned t = 0; t < nthreads; t++) {
+                uint64_t c = M.cnt[(uint64_t)t * M.K + q];
+                M.cnt[(uint64_t)t * M.K + q] = pos;
+                pos += c;
+            }
+        }
+        M.prow[M.K] = pos;
+        or_run(&M, or_task_scatter);
+        g_B = W->B;
+        or_run(&M, or_task_sort);
+        or_run(&M, or_task_insert);
+        for (unsigned t = 0; t < nthreads; t++) {
+            if (M.tstatus[t]) status = M.tstatus[t];
+            if (st) {
+                st->xor_steps += M.tstats[t].xor_steps;
+                st->inserted += M.tstats[t].inserted;
+                if (M.tstats[t].max_drift > st->max_drift) st->max_drift = M.tstats[t].max_drift;
+            }
+        }
+        /* bumped rows in partition order, as the serial insertion emits them */
+        for (uint64_t q = 0; q < M.K; q++) {
+            memmove(bumped_keys + *nbumped, bumped_keys + M.prow[q], sizeof(uint64_t) * M.pbumped[q]);
+            memmove(bumped_vals + *nbumped, bumped_vals + M.prow[q], sizeof(uint32_t) * M.pbumped[q]);
+            *nbumped += M.pbumped[q];
+        }
+        if (status == 0) or_run(&M, or_task_backsub);
+    }
+    free(M.part_of_bucket); free(M.hashed); free(M.cnt); free(M.prow); free(M.pbumped);
+    free(M.tstats); free(M.tstatus);
+    return status;
+}
+
+/*
  * Build one layer.  keys/vals: n input pairs (vals masked to r bits).
  * m slots, hash seed sigma, cuts[0..ncuts) strictly increasing multiples of B
  * (start slots where a new partition begins; empty = one partition).
@@ -246,6 +579,20 @@ int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                         uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
                         or_stats *st)
 {
+    return or_build_layer_mt(keys, vals, n, r, m, sigma, levels, B, w, cuts, ncuts, fallback, mode,
+                             thresh, texact, z, bumped_keys, bumped_vals, nbumped, st, 1);
+}
+
+/* or_build_layer_mode with the partitions spread over nthreads host threads
+ * (1 = serial).  The result is the same for every nthreads. */
+int or_build_layer_mt(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                      uint32_t r, uint64_t m, uint64_t sigma,
+                      const uint32_t levels[4], uint32_t B, uint32_t w,
+                      const uint64_t *cuts, uint64_t ncuts, int fallback,
+                      uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
+                      uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                      or_stats *st, unsigned nthreads)
+{
     *nbumped = 0;
     if (n == 0 || m == 0) return 0;
     if (w != 64 || m % 64 != 0 || m < w) return OR_EINVAL;
@@ -255,127 +602,64 @@ int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
     if (mode == OR_THRESH_2BIT && forced < 0 && ncuts > 0) return OR_EINVAL;
     if (mode != OR_THRESH_2BIT && mode != OR_THRESH_1PLUS) return OR_EINVAL;
     if (mode == OR_THRESH_1PLUS && (B > 255 || (!fallback && !texact))) return OR_EINVAL;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > OR_MAX_THREADS) nthreads = OR_MAX_THREADS;
     const uint32_t t_forced = mode == OR_THRESH_1PLUS ? w : (forced >= 0 ? levels[forced] : 0);
 
-    /* 1. hash every key to its equation */
-    or_row *rows = (or_row *)malloc(sizeof(or_row) * n);
-    if (!rows) return OR_ENOMEM;
-    for (uint64_t i = 0; i < n; i++) {
-        rows[i].key = keys[i];
-        rows[i].val = vals[i] & mask;
-        or_hash(keys[i], sigma, m, w, &rows[i].start, &rows[i].coeff);
-    }
-    /* 2. sort by start slot (bucket asc, offset desc) */
-    g_B = B;
-    qsort(rows, n, sizeof(or_row), or_row_cmp);
-
-    uint64_t *C = (uint64_t *)calloc(m, sizeof(uint64_t));
-    uint32_t *Y = (uint32_t *)calloc(m, sizeof(uint32_t));
-    int64_t *slot_of = (int64_t *)malloc(sizeof(int64_t) * n);
-    if (!C || !Y || !slot_of) { free(rows); free(C); free(Y); free(slot_of); return OR_ENOMEM; }
-    if (!fallback && mode == OR_THRESH_2BIT) {
-        /* every bucket that starts a partition j >= 1 carries the forced level,
-         * also when no key falls into it */
-        memset(thresh, 0, sizeof(uint64_t) * ((nb + 31) / 32));
-        for (uint64_t q = 0; q < ncuts; q++) {
-            uint64_t b = cuts[q] / B;
-            if (b < nb) thresh[b / 32] |= (uint64_t)forced << (2 * (b % 32));
-        }
-    }
-    if (!fallback && mode == OR_THRESH_1PLUS) {
-        memset(texact, 0, nb);
-        for (uint64_t q = 0; q < ncuts; q++) {
-            uint64_t b = cuts[q] / B;
-            if (b < nb) texact[b] = (uint8_t)w;
-        }
-    }
-
-    /* 3. insertion, bucket by bucket */
-    uint64_t i = 0, cut_idx = 0;
+    or_work W;
+    memset(&W, 0, sizeof(W));
+    W.n = n; W.m = m; W.nb = nb; W.r = r; W.B = B; W.w = w; W.mode = mode;
+    W.fallback = fallback; W.forced = forced; W.t_forced = t_forced; W.levels = levels;
+    W.cuts = cuts; W.ncuts = fallback ? 0 : ncuts;
+    W.rows = (or_row *)malloc(sizeof(or_row) * n);
+    W.C = (uint64_t *)calloc(m, sizeof(uint64_t));
+    W.Y = (uint32_t *)calloc(m, sizeof(uint32_t));
+    W.slot_of = (int64_t *)malloc(sizeof(int64_t) * n);
+    W.code_of = (uint8_t *)calloc(nb + 1, 1);
+    W.texact = mode == OR_THRESH_1PLUS && !fallback ? texact : NULL;
+    W.Zs = (uint32_t *)calloc(m + 64, sizeof(uint32_t));
     int status = 0;
-    while (i < n) {
-        uint64_t b = rows[i].start / B;
-        uint64_t j = i;
-        while (j < n && rows[j].start / B == b) j++;
-        /* rows[i..j) is bucket b in descending offset order */
-        while (cut_idx < ncuts && cuts[cut_idx] < b * B) cut_idx++;
-        int after_cut = (cut_idx < ncuts && cuts[cut_idx] == b * B);
-        uint32_t t = (after_cut && !fallback) ? t_forced : 0;
-        uint32_t code = (after_cut && !fallback && mode == OR_THRESH_2BIT) ? (uint32_t)forced : 0;
-        for (uint64_t k = i; k < j; k++) slot_of[k] = -1;
-        for (uint64_t k = i; k < j; k++) {
-            uint32_t off = (uint32_t)(rows[k].start % B);
-            if (off < t) break;              /* forced bump below the level */
-            int64_t p = or_insert(C, Y, rows[k].start, rows[k].coeff, rows[k].val,
-                                  st ? &st->xor_steps : &(uint64_t){0});
-            if (st) st->inserted++;
-            if (p >= 0) {
-                slot_of[k] = p;
-                if (st && (uint64_t)p - rows[k].start > st->max_drift)
-                    st->max_drift = (uint64_t)p - rows[k].start;
-                continue;
-            }
-            if (fallback) { status = OR_FAIL; break; }
-            if (mode == OR_THRESH_1PLUS) {
-                t = off + 1;                 /* rows at offsets >= t were all kept */
-            } else {
-                code = or_level_above(levels, off);
-                if (after_cut && code < (uint32_t)forced) code = (uint32_t)forced;
-                t = levels[code];
-            }
-            /* roll back every row of this bucket below the new threshold */
-            for (uint64_t q = i; q < k; q++) {
-                uint32_t oq = (uint32_t)(rows[q].start % B);
-                if (oq < t && slot_of[q] >= 0) {
-                    C[slot_of[q]] = 0;
-                    Y[slot_of[q]] = 0;
-                    slot_of[q] = -1;
-                }
-            }
-            break;
-        }
-        if (status) break;
-        if (!fallback) {
-            if (mode == OR_THRESH_1PLUS) {
-                texact[b] = (uint8_t)t;
-            } else {
-                thresh[b / 32] &= ~(3ULL << (2 * (b % 32)));
-                thresh[b / 32] |= (uint64_t)code << (2 * (b % 32));
-            }
-            for (uint64_t k = i; k < j; k++) {
-                if ((uint32_t)(rows[k].start % B) < t) {
-                    bumped_keys[*nbumped] = rows[k].key;
-                    bumped_vals[*nbumped] = rows[k].val;
-                    (*nbumped)++;
-                }
-            }
-        }
-        i = j;
-    }
+    if (!W.rows || !W.C || !W.Y || !W.slot_of || !W.code_of || !W.Zs) status = OR_ENOMEM;
 
-    /* 4. back-substitution, right to left, free slots fixed to 0 (READING:
-     * the paper is silent on free variables).  Per-slot r-bit values first,
-     * then packed into bit planes. */
-    if (status == 0) {
-        uint32_t *Zs = (uint32_t *)calloc(m + 64, sizeof(uint32_t));
-        if (!Zs) status = OR_ENOMEM;
-        else {
-            for (uint64_t s = m; s-- > 0;) {
-                if (C[s] == 0) { Zs[s] = 0; continue; }
-                uint32_t v = Y[s];
-                for (int k = 1; k < 64; k++)
-                    if ((C[s] >> k) & 1ULL) v ^= Zs[s + (uint64_t)k];
-                Zs[s] = v;
-            }
-            memset(z, 0, sizeof(uint64_t) * (m / 64) * r);
-            for (uint64_t s = 0; s < m; s++)
-                for (uint32_t k = 0; k < r; k++)
-                    if ((Zs[s] >> k) & 1u)
-                        z[(s / 64) * r + k] |= 1ULL << (s % 64);
-            free(Zs);
+    /* every bucket that starts a partition j >= 1 carries the forced
+     * threshold, also when no key falls into it */
+    if (status == 0 && !fallback) {
+        if (W.texact) memset(W.texact, 0, nb);
+        for (uint64_t q = 0; q < ncuts; q++) {
+            uint64_t b = cuts[q] / B;
+            if (b >= nb) continue;
+            if (W.texact) W.texact[b] = (uint8_t)w;
+            else W.code_of[b] = (uint8_t)forced;
         }
     }
-    free(rows); free(C); free(Y); free(slot_of);
+    if (status == 0 && nthreads == 1) {
+        /* 1. hash every key to its equation */
+        for (uint64_t i = 0; i < n; i++) {
+            W.rows[i].key = keys[i];
+            W.rows[i].val = vals[i] & mask;
+            or_hash(keys[i], sigma, m, w, &W.rows[i].start, &W.rows[i].coeff);
+        }
+        /* 2. sort by start slot (bucket asc, offset desc) */
+        g_B = B;
+        qsort(W.rows, n, sizeof(or_row), or_row_cmp);
+        /* 3. insertion, bucket by bucket */
+        status = or_insert_rows(&W, 0, n, bumped_keys, bumped_vals, nbumped, st);
+        /* 4. back-substitution, then the table's bit planes */
+        if (status == 0) {
+            or_backsub_slots(&W, 0, m);
+            or_pack_planes(&W, 0, m, z);
+        }
+    } else if (status == 0) {
+        status = or_layer_steps_mt(&W, keys, vals, mask, sigma, nthreads, z, bumped_keys, bumped_vals,
+                                   nbumped, st);
+    }
+    /* 2-bit codes, 32 per word: bucket b in bits [2(b%32), 2(b%32)+2) of word b/32 */
+    if (status == 0 && !fallback && mode == OR_THRESH_2BIT) {
+        memset(thresh, 0, sizeof(uint64_t) * ((nb + 31) / 32));
+        for (uint64_t b = 0; b < nb; b++)
+            thresh[b / 32] |= (uint64_t)W.code_of[b] << (2 * (b % 32));
+    }
+    free(W.rows); free(W.C); free(W.Y); free(W.slot_of); free(W.code_of); free(W.Zs);
     return status;
 }
 
@@ -490,6 +774,14 @@ void or_free(or_struct *s)
 int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
              const or_params *p, or_struct *out, or_stats *st)
 {
+    return or_build_mt(keys, vals, n, p, out, st, 1);
+}
+
+/* or_build with each bumping layer's partitions spread over nthreads host
+ * threads (1 = serial); the result is the same for every nthreads. */
+int or_build_mt(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                const or_params *p, or_struct *out, or_stats *st, unsigned nthreads)
+{
     memset(out, 0, sizeof(*out));
     if (p->r < 1 || p->r > 32 || p->w != 64 || p->B % 64 != 0 || p->B < 64 ||
         p->layers > OR_MAX_LAYERS || p->levels[0] != 0 || p->levels[3] != p->B ||
@@ -547,10 +839,10 @@ int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
         uint64_t nb = 0;
         if (!cuts || !L->cuts || !(onep ? (void *)L->texact : (void *)L->thresh) || !L->z) status = OR_ENOMEM;
         else
-            status = or_build_layer_mode(ck, cv, cn, p->r, L->m,
-                                         or_layer_seed(p->seed, l), p->levels, p->B, p->w,
-                                         cuts, ncuts, 0, p->threshold_mode, L->thresh, L->texact,
-                                         L->z, nk, nv, &nb, st);
+            status = or_build_layer_mt(ck, cv, cn, p->r, L->m,
+                                       or_layer_seed(p->seed, l), p->levels, p->B, p->w,
+                                       cuts, ncuts, 0, p->threshold_mode, L->thresh, L->texact,
+                                       L->z, nk, nv, &nb, st, nthreads);
         free(cuts);
         L->nbumped = nb;
         if (st) st->bumped[l] = nb;

@@ -11,6 +11,7 @@
 #define OR_ENOMEM (-2)
 #define OR_UNSOLVABLE (-3)
 #define OR_FAIL (-4)
+#define OR_MAX_THREADS 256     /* host threads of the threaded variants */
 
 #define OR_THRESH_2BIT 0u   /* four threshold levels, 2 bits per bucket */
 #define OR_THRESH_1PLUS 1u  /* exact threshold; 1 bit per bucket + the bumping buckets' thresholds */
@@ -87,11 +88,20 @@ int or_build_layer_mode(const uint64_t *keys, const uint32_t *vals, uint64_t n,
                         uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
                         uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
                         or_stats *st);
+int or_build_layer_mt(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                      uint32_t r, uint64_t m, uint64_t sigma,
+                      const uint32_t levels[4], uint32_t B, uint32_t w,
+                      const uint64_t *cuts, uint64_t ncuts, int fallback,
+                      uint32_t mode, uint64_t *thresh, uint8_t *texact, uint64_t *z,
+                      uint64_t *bumped_keys, uint32_t *bumped_vals, uint64_t *nbumped,
+                      or_stats *st, unsigned nthreads);
 int or_search_cuts(const uint64_t *keys, uint64_t n, uint64_t m, uint64_t sigma, uint32_t B, uint32_t w,
                    uint64_t P, uint64_t K, uint32_t mode, uint32_t range, uint64_t *cuts);
 void or_default_params(or_params *p);
 int or_build(const uint64_t *keys, const uint32_t *vals, uint64_t n,
              const or_params *p, or_struct *out, or_stats *st);
+int or_build_mt(const uint64_t *keys, const uint32_t *vals, uint64_t n,
+                const or_params *p, or_struct *out, or_stats *st, unsigned nthreads);
 void or_free(or_struct *s);
 uint32_t or_query_one(const or_struct *s, uint64_t key);
 void or_query(const or_struct *s, const uint64_t *keys, uint32_t *out, uint64_t n);

@@ -40,7 +40,7 @@ def build_lib(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -98,6 +98,9 @@ def lib():
             L.or_build_layer_mode.restype = C.c_int
             L.or_build_layer_mode.argtypes = [p, p, u64, u32, u64, u64, p, u32, u32, p, u64, C.c_int,
                                               u32, p, p, p, p, p, C.POINTER(u64), C.POINTER(Stats)]
+            L.or_build_layer_mt.restype = C.c_int
+            L.or_build_layer_mt.argtypes = [p, p, u64, u32, u64, u64, p, u32, u32, p, u64, C.c_int,
+                                            u32, p, p, p, p, p, C.POINTER(u64), C.POINTER(Stats), C.c_uint]
             L.or_search_cuts.restype = C.c_int
             L.or_search_cuts.argtypes = [p, u64, u64, u64, u32, u32, u64, u64, u32, u32, p]
             L.or_struct_size.restype = u64; L.or_struct_size.argtypes = []
@@ -106,6 +109,9 @@ def lib():
             L.or_default_params.restype = None; L.or_default_params.argtypes = [C.POINTER(Params)]
             L.or_build.restype = C.c_int
             L.or_build.argtypes = [p, p, u64, C.POINTER(Params), C.POINTER(Struct), C.POINTER(Stats)]
+            L.or_build_mt.restype = C.c_int
+            L.or_build_mt.argtypes = [p, p, u64, C.POINTER(Params), C.POINTER(Struct), C.POINTER(Stats),
+                                      C.c_uint]
             L.or_free.restype = None; L.or_free.argtypes = [C.POINTER(Struct)]
             L.or_query.restype = None; L.or_query.argtypes = [C.POINTER(Struct), p, p, u64]
             L.or_export.restype = u64; L.or_export.argtypes = [C.POINTER(Struct), p, u64]
@@ -183,9 +189,10 @@ class LayerResult:
 
 
 def build_layer(keys, vals, r, m, sigma, cuts=(), fallback=False,
-                levels=(0, 32, 64, 128), B=128, w=64, mode=THRESH_2BIT) -> LayerResult:
+                levels=(0, 32, 64, 128), B=128, w=64, mode=THRESH_2BIT, threads=1) -> LayerResult:
     """One layer with an explicit cut list (start slots of partitions 1..K-1).
-    mode THRESH_1PLUS gives exact per-bucket thresholds in .texact."""
+    mode THRESH_1PLUS gives exact per-bucket thresholds in .texact.  threads > 1
+    spreads the partitions over host threads (same result)."""
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     vals = np.ascontiguousarray(vals, dtype=np.uint32)
     n = len(keys)
@@ -199,7 +206,12 @@ def build_layer(keys, vals, r, m, sigma, cuts=(), fallback=False,
     nbumped = C.c_uint64()
     st = Stats()
     texact = np.zeros(nb + 1, dtype=np.uint8)
-    if mode == THRESH_2BIT:
+    if threads > 1:
+        rc = lib().or_build_layer_mt(_ptr(keys), _ptr(vals), n, r, m, sigma, _ptr(lv), B, w,
+                                     _ptr(cu), len(cuts), int(fallback), mode, _ptr(thresh),
+                                     _ptr(texact), _ptr(z), _ptr(bk), _ptr(bv), C.byref(nbumped),
+                                     C.byref(st), threads)
+    elif mode == THRESH_2BIT:
         rc = lib().or_build_layer(_ptr(keys), _ptr(vals), n, r, m, sigma, _ptr(lv), B, w,
                                   _ptr(cu), len(cuts), int(fallback), _ptr(thresh), _ptr(z),
                                   _ptr(bk), _ptr(bv), C.byref(nbumped), C.byref(st))
@@ -216,14 +228,18 @@ def build_layer(keys, vals, r, m, sigma, cuts=(), fallback=False,
 class OracleStruct:
     """A built structure: per-layer sizes, thresholds and tables, export and query."""
 
-    def __init__(self, keys, vals, params: Params):
+    def __init__(self, keys, vals, params: Params, threads: int = 1):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         vals = np.ascontiguousarray(vals, dtype=np.uint32)
         self._s = Struct()
         self.stats = Stats()
         self.params = params
-        self.status = lib().or_build(_ptr(keys), _ptr(vals), len(keys), C.byref(params),
-                                     C.byref(self._s), C.byref(self.stats))
+        if threads > 1:
+            self.status = lib().or_build_mt(_ptr(keys), _ptr(vals), len(keys), C.byref(params),
+                                            C.byref(self._s), C.byref(self.stats), threads)
+        else:
+            self.status = lib().or_build(_ptr(keys), _ptr(vals), len(keys), C.byref(params),
+                                         C.byref(self._s), C.byref(self.stats))
 
     def __del__(self):
         try:
@@ -274,8 +290,10 @@ class OracleStruct:
         return out[:len(keys)]
 
 
-def build(keys, vals, **params) -> OracleStruct:
-    return OracleStruct(keys, vals, default_params(**params))
+def build(keys, vals, threads: int = 1, **params) -> OracleStruct:
+    """The whole structure; threads > 1 spreads each bumping layer's partitions
+    over host threads (the paper's parallel construction; same result)."""
+    return OracleStruct(keys, vals, default_params(**params), threads=threads)
 
 
 def search_cuts(keys, m, sigma, P, K, mode, search_range, B=128, w=64) -> np.ndarray:

@@ -47,8 +47,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     mut = tmp_path / "mut.c"
     mut.write_text(src.replace(old, new))
     lib = tmp_path / "libmut.so"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-I", os.path.join(ROOT, "oracle"),
-                           "-o", str(lib), str(mut), "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-I",
+                           os.path.join(ROOT, "oracle"), "-o", str(lib), str(mut), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(lib))
     pins = ["tests/test_oracle_hash.py", "tests/test_oracle_bruteforce.py", "tests/test_oracle_invariants.py",
             "tests/test_oracle_cut_search.py"]
