@@ -153,11 +153,19 @@ typedef void *(*burr_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
 typedef void (*burr_free_fn)(void *ptr, void *stream, void *ctx);
 int burr_set_allocator(burr_alloc_fn alloc, burr_free_fn free, void *ctx);
 
-/* Fill *p with the defaults above.  Returns BURR_OK or BURR_ERR_INVALID (p NULL). */
+/* Fill *p with the defaults above.  Returns BURR_OK or BURR_ERR_INVALID (p NULL).
+ * Defaults follow the paper's setup where it gives one: buckets of 128 and four
+ * bumping layers plus a base case (Sec. 4), 2-bit thresholds (Sec. 2,
+ * "Bumping"), partitions that bump at least w-1 slots after each cut (Sec. 3);
+ * the rest (hash, levels, load factor, P) are this library's readings above. */
 int burr_default_params(burr_params *p);
 
 /*
  * Build the structure for n keys (distinct; S is a set) and their r-bit values.
+ * Paper: the retrieval problem of Sec. 1 (store f: S -> {0,1}^r so that
+ * x in S gives f(x)), built as in Sec. 2 (ribbon equations, bumping by
+ * thresholds, overloading, back-substitution, layers) with the partitioned
+ * parallel construction of Sec. 3 (cuts, w-1 slots bumped after each cut).
  *   keys    n uint64 keys, host or device, caller-owned, read only.
  *   values  n values of the r-bit value type, host or device, caller-owned.
  *   r       value bits, 1..32.
@@ -198,6 +206,12 @@ int burr_build_batch(const uint64_t *keys, const void *values, const uint64_t *o
                      uint32_t count, const burr_params *p, void *stream, burr_handle **out);
 
 /*
+ * Paper: the query of Sec. 2: per layer, a key below its bucket's threshold
+ * continues in the next layer, else its value is the parity of its
+ * coefficient row AND the table window at its start slot, one bit per value
+ * bit; cuts are invisible to queries (Sec. 3, partitions change only which
+ * keys are bumped).  Keys of S return f(x); other keys an arbitrary but
+ * deterministic value (Sec. 1).
  * Query n keys (host or device), writing n values of the handle's value type
  * to out (host or device).  Stream-ordered: with device keys and output the
  * call only enqueues work on `stream`; with any host pointer it copies through
@@ -205,12 +219,14 @@ int burr_build_batch(const uint64_t *keys, const void *values, const uint64_t *o
  */
 int burr_query(const burr_handle *h, const uint64_t *keys, void *out, uint64_t n, void *stream);
 
-/* Bytes of the device tables (Z of every layer + thresholds + a 64-byte header). */
+/* Bytes of the device tables (Z of every layer + thresholds + a 64-byte header):
+ * the space the paper accounts as overhead over r*n bits (Sec. 4.1 and Fig. 3,
+ * overhead per additional thread).  BURR_ERR_INVALID if h or bytes is NULL. */
 int burr_size_bytes(const burr_handle *h, uint64_t *bytes);
 
 /*
  * Canonical little-endian serialisation (checkpoint format and the form in
- * which results are compared bit for bit):
+ * which results are compared bit for bit; the paper has no counterpart):
  *   u32 magic 0x52525542, u32 version (1: 2-bit, 2: 1+-bit thresholds),
  *   u32 r, u32 w, u32 B, u32 layers,
  *   u32 levels[4], u64 seed, u64 bits of load_factor, u64 n, u64 partition_slots,
@@ -243,9 +259,14 @@ int burr_export(const burr_handle *h, void *host_buf, uint64_t *len);
  */
 int burr_import(const void *host_buf, uint64_t len, void *stream, burr_handle **out);
 
+/* Sizes per layer (n, m, partitions, bumped keys: the quantities of Sec. 2-3),
+ * device time per stage (the split of Fig. 7: sort, insertion with bumping,
+ * back-substitution) and launch count of a build.  The call itself has no
+ * counterpart in the paper.  BURR_ERR_INVALID if h or st is NULL. */
 int burr_stats(const burr_handle *h, burr_stats_t *st);
 
-/* Release the handle and its device memory (NULL is ignored). */
+/* Release the handle and its device memory (NULL is ignored).  The paper has
+ * no counterpart (a library's resource management). */
 void burr_free(burr_handle *h);
 
 /* burr_free of handles[0 .. count) in one call (NULL entries are ignored),
@@ -253,6 +274,9 @@ void burr_free(burr_handle *h);
  * by the caller; the handles must not be used afterwards. */
 void burr_free_many(burr_handle *const *handles, uint64_t count);
 
+/* Name of a BURR_* status code, and the message of the calling thread's last
+ * failed call (both library conveniences with no counterpart in the paper;
+ * the strings are owned by the library). */
 const char *burr_strerror(int code);
 const char *burr_last_error(void);
 
@@ -292,9 +316,10 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
  *   BURR_ERR_INVALID with a message.
  *   The sort's scratch is one fixed file-scope device array of about 12.6 MB
  *   that every GPU which loads the library keeps until the process exits.
- *   The first call on a device looks up that array's device address (once per
- *   device, with the device current); make that first call before any stream
- *   capture.  All calls share the array and it keeps the last call's
+ *   Every call looks up that array's device address with the device current
+ *   (a lookup that allocates nothing); the first call on a device also loads
+ *   the library's device code there, so make that first call before any
+ *   stream capture.  All calls share the array and it keeps the last call's
  *   contents: calls whose work overlaps on the GPU (other streams or host
  *   threads) race, so order them, e.g. on one stream.
  */

@@ -1388,7 +1388,10 @@ int import_into(const uint8_t *buf, uint64_t len, cudaStream_t st, burr_handle *
     uint64_t cur = n;
     for (uint32_t l = 0; l < p.layers; ++l) {
         if (ln[l] != cur || lm[l] % 64 || lm[l] >= (1ull << 32) || lb[l] != num_buckets(lm[l], p.bucket_slots) ||
-            lbump[l] > ln[l] || (ln[l] == 0) != (lm[l] == 0))
+            lbump[l] > ln[l] || (ln[l] == 0) != (lm[l] == 0) ||
+            // partitions: none in an empty layer, otherwise at least one and at
+            // most one per bucket (each partition starts at its own bucket)
+            (lm[l] == 0 ? lk[l] != 0 : (lk[l] == 0 || lk[l] > lb[l])))
             return fail(BURR_ERR_INVALID, "export layer %u sizes are inconsistent", l);
         cur = lbump[l];
     }

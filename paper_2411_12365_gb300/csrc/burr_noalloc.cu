@@ -13,7 +13,6 @@
 // GPU (different streams, or different host threads) race on it: the caller
 // must order them, e.g. by issuing them on one stream.
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "burr_internal.cuh"
@@ -36,28 +35,21 @@ constexpr size_t kScratchBytes = align256(kNoAllocMaxKeys * 8) + align256(kNoAll
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_sort_scratch on the current device, looked up once per
-// device.  In host code the array's name is only a host-side stand-in, so the
-// kernels must be given this address instead.
+// Device address of g_sort_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the kernels must be given this
+// address instead.  It is looked up on every call (a table lookup that
+// allocates nothing), so a context rebuilt after cudaDeviceReset gets its own
+// array's address rather than a stale one; the first call on a device also
+// loads the library's device code there.
 int scratch_on_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return burr::set_error(BURR_ERR_CUDA, (std::string("cudaGetDevice: ") + cudaGetErrorString(e)).c_str());
-    if (dev < 0 || dev >= kMaxDevices) return burr::set_error(BURR_ERR_INVALID, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess || !p)
-            return burr::set_error(BURR_ERR_CUDA,
-                                   (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || !p)
+        return burr::set_error(BURR_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+    *out = p;
     return BURR_OK;
 }
 

@@ -61,6 +61,9 @@ def test_malformed_exports_are_rejected(burr, mode):
         "layer-0 keys": _patch(good, hdr, "<Q", 19_999),
         "layer-0 slots": _patch(good, hdr + 8, "<Q", 12345),
         "base-case seed index": _patch(good, hdr + 4 * 40 + 16, "<Q", 99),
+        "layer-0 no partitions": _patch(good, hdr + 16, "<Q", 0),
+        "layer-0 more partitions than buckets": _patch(
+            good, hdr + 16, "<Q", struct.unpack_from("<Q", good, hdr + 24)[0] + 1),
     }
     if mode == O.THRESH_1PLUS:
         # first threshold section follows the base-case record
