@@ -1,19 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark of the GB300 BuRR hot path: one step = build a BuRR structure of n
-keys (hash, sort by bucket, band + bump with partition cuts, back-substitution,
-recursion into the next layers and the base case) and query n keys (half of
-them members, half not), all through the C ABI of libburr.so.
+"""Benchmark of the GB300 BuRR hot path: one step = construction of a BuRR
+structure of n keys (hash, sort by bucket, band + bump with partition cuts,
+back-substitution, recursion into the next layers and the base case) through
+the C ABI of libburr.so.
 
-Default workload: 10^8 uniform-random 64-bit keys, r = 8 (8-bit filter
-values), w = 64, partitions of 2^16 slots, plus 10^8 queries.
+Default workload: 10^9 uniform-random 64-bit keys, r = 8 (8-bit filter
+values), w = 64, 2-bit thresholds, partitions of 2^16 slots in layer 0 and
+4096 in deeper layers.  Queries (n keys, half members) are timed apart, and
+the same construction at r = 1 and r = 16 gives the per-stage split.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl burr|reference]
 
-Prints one JSON line (rank 0).  `value` is keys per second through the whole
-step, device-resident inputs; `e2e` is the same with the inputs in pinned host
-memory and the copies inside the timed region; `roofline` is the dominant
-kernel (layer-0 band + bump) against the measured HBM bandwidth;
-`cpu_baseline` is the serial CPU oracle on a bounded sample.
+Prints one JSON line (rank 0).  `value` is constructed keys per second with
+device-resident inputs; `e2e` is the construction from page-locked host keys
+and values with the structure read back to the host, copies inside the timed
+region; `roofline` is the dominant kernel (layer-0 band + bump) against the
+measured HBM bandwidth; `cpu_baseline` is the CPU oracle on a bounded sample,
+serial and with its partitions spread over the host's cores.
 """
 from __future__ import annotations
 
@@ -40,7 +43,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="burr", choices=["burr", "reference"])
-    ap.add_argument("--keys", type=int, default=100_000_000, help="keys per structure")
+    ap.add_argument("--keys", type=int, default=1_000_000_000, help="keys per structure")
     ap.add_argument("--r", type=int, default=8)
     ap.add_argument("--partition-slots", type=int, default=65536)
     ap.add_argument("--lower-partition-slots", type=int, default=4096)
@@ -51,8 +54,14 @@ def args_():
                     help="threshold storage: 2-bit levels or 1+-bit (bit per bucket + exact thresholds)")
     ap.add_argument("--min-partition-slots", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
-                    help="keys of the oracle sample (about 12 s of serial CPU work)")
-    ap.add_argument("--ref-sample", type=int, default=1 << 20, help="keys per reference-arm step")
+                    help="keys of the serial oracle sample (about 10 s of CPU work)")
+    ap.add_argument("--cpu-sample-mt", type=int, default=1 << 26,
+                    help="keys of the threaded oracle sample (all host cores)")
+    ap.add_argument("--ref-sample", type=int, default=1 << 24, help="keys per reference-arm step")
+    ap.add_argument("--ref-threads", type=int, default=0,
+                    help="host threads of the reference arm's oracle (0 = all cores)")
+    ap.add_argument("--split-r", default="1,16",
+                    help="value widths whose construction split (sort/band/back-substitution) is also reported")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-steps", action="store_true",
@@ -80,10 +89,11 @@ def measured_peaks():
 
 
 def ncu_band_summary(kernel_src: str, path: str | None = None):
-    """Per-launch DRAM bytes and warp instructions of the 10^8-key layer-0 band
-    launch (2-bit thresholds, 1-byte values) from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    path = path or os.path.join(ROOT, "profiles", "k_band_1e8_r8_traffic.txt")
+    """DRAM bytes and warp instructions of one captured layer-0 band launch
+    (2-bit thresholds, 1-byte values) and its layer-0 key count, from the
+    committed ncu summary, if it was taken on the current kernel source; else
+    None.  Both grow in proportion to the keys of the launch."""
+    path = path or os.path.join(ROOT, "profiles", "k_band_2e25_r8_traffic.txt")
     try:
         kv = {}
         for line in open(path):
@@ -93,9 +103,10 @@ def ncu_band_summary(kernel_src: str, path: str | None = None):
         src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         if kv.get("kernel_source_sha256_16") != src_hash:
             return None
-        inst = kv.get("warp_instructions_per_launch_scaled")
-        return {"dram_bytes": float(kv["dram_bytes_per_launch_scaled"]),
-                "warp_instructions": float(inst) if inst else None}
+        inst = kv.get("warp_instructions_captured")
+        return {"dram_bytes": float(kv["dram_bytes_per_launch_captured"]),
+                "warp_instructions": float(inst) if inst else None,
+                "keys": float(kv["n_keys_captured"])}
     except Exception:
         return None
 
@@ -189,21 +200,21 @@ def max_over_ranks(pg, x: float) -> float:
 
 
 def oracle_sample(n_s: int, r: int, P: int, minP: int = 4096, lowP: int = 4096, mode: int = 0, cut: int = 0,
-                  cut_range: int = 50):
-    """Serial CPU oracle: build + query of n_s keys; returns (seconds, n_s)."""
+                  cut_range: int = 50, threads: int = 1):
+    """CPU oracle: construction of n_s keys of the workload (serial, or with each
+    layer's partitions over `threads` host threads); returns seconds."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_2411_12365_gb300 import inputs as I
     k = I.keys_np(n_s)
     v = I.values_np(k, r).astype(np.uint32)
-    q = np.concatenate([k[: n_s // 2], I.keys_np(n_s - n_s // 2, offset=n_s)])
     t0 = time.perf_counter()
     s = O.build(k, v, r=r, partition_slots=P, min_partition_slots=minP, lower_partition_slots=lowP,
-                threshold_mode=mode, cut_search=cut, cut_search_range=cut_range)
-    out = s.query(q)
+                threshold_mode=mode, cut_search=cut, cut_search_range=cut_range, threads=threads)
     dt = time.perf_counter() - t0
-    assert s.ok and np.array_equal(out[: n_s // 2], v[: n_s // 2])
+    sel = np.arange(0, n_s, max(1, n_s // 4096))
+    assert s.ok and np.array_equal(s.query(k[sel]), v[sel])
     oracle_sample.xor_steps_per_row = s.stats.xor_steps / max(s.stats.inserted, 1)
     return dt
 
@@ -214,22 +225,25 @@ def run_reference(a, ws, rank, pg):
     from oracle import oracle as O
     O.build_lib()
     n_s = a.ref_sample
-    for _ in range(a.warmup):
-        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a),
-                      cmode(a), a.cut_search_range)
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a),
-                      cmode(a), a.cut_search_range)
-    dt = (time.perf_counter() - t0) / a.steps
+    cores, model = cpu_info()
+    threads = a.ref_threads or cores
+    dt = 0.0
+    for i in range(a.warmup + a.steps):
+        t = oracle_sample(n_s, a.r, a.partition_slots, a.min_partition_slots, a.lower_partition_slots, tmode(a),
+                          cmode(a), a.cut_search_range, threads=threads)
+        if i >= a.warmup:
+            dt += t
+    dt /= max(a.steps, 1)
     value = n_s / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(a),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"serial C oracle: build + query of {n_s} keys per step (of the {a.keys}-key workload)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"C oracle with each layer's partitions spread over {threads} host threads: "
+                                   f"construction of {n_s} keys per step (of the {a.keys}-key workload)",
+                         "nproc": cores, "cpu_model": model},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,11 +261,10 @@ def workload_config(a):
     tdesc = "1+-bit thresholds" if a.thresholds == "1plus" else "2-bit thresholds"
     if a.cut_search != "none":
         tdesc += f", {a.cut_search} cut search over {a.cut_search_range} buckets"
-    return {"workload": f"{a.keys} uniform-random 64-bit keys, r={a.r}, w=64, {tdesc}, "
-                        f"partition size {a.partition_slots} slots in layer 0 and {a.lower_partition_slots} "
-                        f"in deeper layers, plain build + {a.keys} queries "
-                        f"(half members, half non-members)",
-            "n_keys": a.keys, "queries": a.keys, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
+    return {"workload": f"construction of one structure of {a.keys} uniform-random 64-bit keys, r={a.r}, w=64, "
+                        f"{tdesc}, partition size {a.partition_slots} slots in layer 0 and "
+                        f"{a.lower_partition_slots} in deeper layers, 4 layers + base case, plain build",
+            "n_keys": a.keys, "r": a.r, "ribbon_width": 64, "bucket_slots": 128,
             "partition_slots": a.partition_slots, "lower_partition_slots": a.lower_partition_slots,
             "min_partition_slots": a.min_partition_slots, "load_factor": 1.015, "layers": 4,
             "thresholds": a.thresholds, "cut_search": a.cut_search, "cut_search_range": a.cut_search_range,
@@ -503,18 +516,47 @@ def run_served(a, ws, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
-def main():
-    a = args_()
-    ws, rank, local, pg = dist_setup()
-    if a.impl == "reference":
-        run_reference(a, ws, rank, pg)
-        return
-    if a.workload == "batched":
-        run_batched(a, ws, rank, local, pg)
-        return
-    if a.workload == "serve":
-        run_served(a, ws, rank, local, pg)
-        return
+def cpu_info():
+    """Host cores and CPU model (for the CPU-baseline record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def stage_split(stats_list, layers):
+    """Mean device ms per layer and stage (sort, band + bump, back-substitution)
+    over several builds, and the layer-0 stages."""
+    avg = lambda f: statistics.mean(f(s) for s in stats_list)  # noqa: E731
+    per_layer = [[round(avg(lambda s, l=l, k=k: s["stage_ms"][l][k]), 4) for k in range(3)]
+                 for l in range(layers + 1)]
+    return {"build_ms": avg(lambda s: s["total_ms"]),
+            "layer0_ms": {"sort": per_layer[0][0], "band_bump": per_layer[0][1], "backsub": per_layer[0][2]},
+            "stage_ms_per_layer [sort, band+bump, backsub]": per_layer}
+
+
+def compulsory_build_bytes(st, r):
+    """Compulsory bytes of a build (the model of the roofline): per layer-l key
+    read (key, value) and one partition-order round trip, bumped keys written
+    into the next layer, the table written once."""
+    vb = 1 if r <= 8 else (2 if r <= 16 else 4)
+    layers = st["layers"]
+    ln, lm = st["layer_n"], st["layer_m"]
+    return (sum(ln[:layers + 1]) * 3 * (8 + vb) + sum(ln[1:layers + 1]) * (8 + vb)
+            + sum(lm[:layers + 1]) * r // 8)
+
+
+def run_plain(a, ws, rank, local, pg):
     import numpy as np
     import torch
 
@@ -528,30 +570,32 @@ def main():
     seed = I.KEY_SEED + rank * 0x100000000        # independent structure per rank
     keys = I.keys_torch(n, dev, seed=seed)
     vals = I.values_torch(keys, r)
-    half = n // 2
-    qkeys = torch.cat([keys[:half], I.keys_torch(n - half, dev, seed=seed, offset=n)])
-    qout = torch.empty(n, dtype=burr.value_torch_dtype(r), device=dev)
-    params = burr.default_params(partition_slots=P, min_partition_slots=a.min_partition_slots,
-                                 lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a),
-                                 cut_search=cmode(a), cut_search_range=a.cut_search_range, flags=burr.FLAG_TIMING)
-    torch.cuda.synchronize()
 
+    def params_for(flags=burr.FLAG_TIMING):
+        return burr.default_params(partition_slots=P, min_partition_slots=a.min_partition_slots,
+                                   lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a),
+                                   cut_search=cmode(a), cut_search_range=a.cut_search_range, flags=flags)
+
+    params = params_for()
+    torch.cuda.synchronize()
     stats_acc = []
     launches = [0]
 
     def step():
+        # one construction: hash, sort, band + bump, back-substitution of every
+        # layer and the base case; the handle is released right after
         h = burr.build(keys, vals, r, params=params)
-        h.query(qkeys, out=qout)
         st = h.stats()
         stats_acc.append(st)
-        launches[0] += st["kernel_launches"] + 1
+        launches[0] += st["kernel_launches"]
         h.free()
 
     for _ in range(a.warmup):
         step()
-    # correctness of the timed configuration (again after the timed steps)
-    if a.warmup:
-        assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
+    # correctness of the timed configuration: query(x) = f(x) for every key
+    h = burr.build(keys, vals, r, params=params)
+    assert torch.equal(h.query(keys), vals), "query(x) != f(x)"
+    h.free()
     stats_acc.clear()
     launches[0] = 0
     torch.cuda.synchronize()
@@ -567,103 +611,132 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
     barrier(pg)
-    assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
-    ms = ev0.elapsed_time(ev1) / a.steps
-    ms = max_over_ranks(pg, ms)
+    ms = max_over_ranks(pg, ev0.elapsed_time(ev1) / a.steps)
     value = ws * n / (ms / 1e3) / 1e6
     if a.profile_steps:
         if rank == 0:
             print(json.dumps({"ms_per_step": ms, "value": value}))
         return
 
-    # per-stage device times (layer 0 dominates)
     st0 = stats_acc[-1]
     layers = st0["layers"]
-    avg = lambda f: statistics.mean(f(s) for s in stats_acc)  # noqa: E731
-    band0 = avg(lambda s: s["stage_ms"][0][1])
-    sort0 = avg(lambda s: s["stage_ms"][0][0])
-    bs0 = avg(lambda s: s["stage_ms"][0][2])
-    build_ms = avg(lambda s: s["total_ms"])
+    split = stage_split(stats_acc, layers)
+    band0 = split["layer0_ms"]["band_bump"]
+    build_ms = split["build_ms"]
     n0, m0 = st0["layer_n"][0], st0["layer_m"][0]
     nb0 = (m0 - 64 + 128) // 128
     bump0 = st0["layer_bumped"][0]
-    band_bytes = n0 * (8 + vb) + (nb0 + 1) * 4 + m0 * (8 + vb) + bump0 * (8 + vb) + ((nb0 + 31) // 32) * 8
+    # algorithmic bytes of the layer-0 band launch: read the bucket-sorted
+    # (key, value) records, write the bumped ones, write the thresholds
+    band_bytes = n0 * (8 + vb) + bump0 * (8 + vb) + ((nb0 + 31) // 32) * 8
     peak, peak_kind = measured_peaks()
     achieved = band_bytes / (band0 / 1e3) / 1e9
     # the ncu figures belong to the captured instantiation: 2-bit thresholds, 1-byte values
     summ = (ncu_band_summary(os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu"))
             if tmode(a) == 0 and vb == 1 else None)
-    scale = n0 / 1e8                       # the summary is scaled to a 10^8-key launch
+    scale = n0 / summ["keys"] if summ else None
     traffic = summ["dram_bytes"] * scale if summ else None
-    # space overhead: bits of the device tables (Z, thresholds) over r*n
     overhead = (st0["table_bytes"] - 64) * 8 / (r * n) - 1
-    # whole-stage rooflines against compulsory bytes:
-    # build: per layer-l key read (key, value) and one partition-order round
-    # trip, bumped keys written into the next layer, the table written once;
-    # query: the key and the output, per visited layer one threshold sector and
-    # the 2r-word table window in 32-byte sectors
-    ln, lm = st0["layer_n"], st0["layer_m"]
-    build_bytes = (sum(ln[:layers + 1]) * 3 * (8 + vb) + sum(ln[1:layers + 1]) * (8 + vb)
-                   + sum(lm[:layers + 1]) * r // 8)
-    visits = sum(ln[:layers + 1]) / max(ln[0], 1)
+    build_bytes = compulsory_build_bytes(st0, r)
+
+    # queries, timed apart from construction: n keys, half members
+    half = n // 2
+    qkeys = torch.cat([keys[:half], I.keys_torch(n - half, dev, seed=seed, offset=n)])
+    qout = torch.empty(n, dtype=burr.value_torch_dtype(r), device=dev)
+    h = burr.build(keys, vals, r, params=params)
+    qsteps = max(3, min(a.steps, 10))
+    for _ in range(2):
+        h.query(qkeys, out=qout)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record()
+    for _ in range(qsteps):
+        h.query(qkeys, out=qout)
+    q1.record()
+    torch.cuda.synchronize()
+    query_ms = q0.elapsed_time(q1) / qsteps
+    assert torch.equal(qout[:half], vals[:half]), "query(x) != f(x)"
+    visits = sum(st0["layer_n"][:layers + 1]) / max(n0, 1)
     query_bytes = n * (8 + vb) + n * visits * (32 + -(-2 * r * 8 // 32) * 32)
-    query_ms = ms - build_ms
-    stage_roofline = {
-        "peak_gbs": peak, "peak_kind": peak_kind,
-        "build": {"compulsory_bytes": build_bytes, "achieved_gbs": build_bytes / (build_ms / 1e3) / 1e9,
-                  "frac": build_bytes / (build_ms / 1e3) / 1e9 / peak},
-        "query": {"compulsory_bytes": query_bytes, "achieved_gbs": query_bytes / (query_ms / 1e3) / 1e9,
-                  "frac": query_bytes / (query_ms / 1e3) / 1e9 / peak,
-                  "note": "sectors counted as if from DRAM; a table smaller than the 129 MB L2 is mostly served "
-                          "from L2"},
-    }
+    h.free()
+    del qkeys, qout
+    torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": workload_config(a), "wall_s_timed": wall,
         "breakdown": {
-            "build_ms": build_ms, "query_ms": ms - build_ms,
-            "build_mkeys_s": n / build_ms / 1e3, "query_mkeys_s": n / max(ms - build_ms, 1e-9) / 1e3,
-            "layer0_ms": {"sort(4 kernels)": sort0, "band_bump": band0, "backsub": bs0},
-            "stage_ms_per_layer": [[round(x, 4) for x in s] for s in st0["stage_ms"]],
+            "step": "one burr_build of n device-resident keys (all layers and the base case), then burr_free",
+            "build_ms_device": build_ms, "build_mkeys_s": n / build_ms / 1e3,
+            **split,
             "layer_n": st0["layer_n"], "layer_m": st0["layer_m"], "layer_parts": st0["layer_parts"],
             "space_overhead": overhead,
-            "roofline_by_stage": stage_roofline,
+            "query": {"keys": n, "members": half, "ms": query_ms, "mkeys_s": n / query_ms / 1e3,
+                      "compulsory_bytes": query_bytes, "frac": query_bytes / (query_ms / 1e3) / 1e9 / peak,
+                      "note": "timed apart from construction; 32-byte sectors counted as if from DRAM"},
+            "roofline_by_stage": {
+                "peak_gbs": peak, "peak_kind": peak_kind,
+                "build": {"compulsory_bytes": build_bytes,
+                          "achieved_gbs": build_bytes / (ms / 1e3) / 1e9,
+                          "frac": build_bytes / (ms / 1e3) / 1e9 / peak,
+                          "model": "per layer-l key 3(8+v) bytes, bumped keys (8+v) into the next layer, "
+                                   "the table once; over the timed step"}},
             "paper_cpu_context": "67.8 Mkeys/s construction, 1e8 keys, 64 threads on EPYC 7551P (Fig. 7)",
         },
         "roofline": {"bound": "hbm", "kernel": "k_band (layer 0)", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes": band_bytes,
-                     "note": "band+bump is latency-bound (dependent GF(2) elimination chains)"},
+                     "algorithmic_model": "read n0 sorted (key, value) records, write the bumped ones, "
+                                          "write the 2-bit thresholds",
+                     "note": "band+bump is latency-bound (dependent GF(2) elimination chains); see issue"},
         "gpu_launches": launches[0],
     }
     line["clocks"] = clk.summary()
     if summ and summ["warp_instructions"]:
-        import torch
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = line["clocks"].get("sm_max_mhz") or 2070.0
         line["roofline"]["issue"] = issue_roofline(summ["warp_instructions"] * scale, band0, sms, mhz)
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # the sort/band/back-substitution split at other value widths (r = 1, 16)
+    if a.split_r and rank == 0:
+        other = {}
+        for rr in (int(x) for x in a.split_r.split(",") if x):
+            v2 = I.values_torch(keys, rr)
+            acc = []
+            for i in range(3 + 5):
+                h = burr.build(keys, v2, rr, params=params)
+                if i >= 3:
+                    acc.append(h.stats())
+                h.free()
+            sp = stage_split(acc, acc[-1]["layers"])
+            sp["build_mkeys_s"] = n / sp["build_ms"] * 1e-3
+            sp["space_overhead"] = (acc[-1]["table_bytes"] - 64) * 8 / (rr * n) - 1
+            other[f"r{rr}"] = sp
+            del v2
+        line["breakdown"]["split_by_r"] = other
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI: keys and values in page-locked host memory,
+    # the structure read back into page-locked host memory, copies inside the timed region
     if not a.no_e2e:
         hk = keys.cpu().pin_memory()
         hv = vals.cpu().pin_memory()
-        hq = qkeys.cpu().pin_memory()
-        ho = torch.empty(n, dtype=qout.dtype).pin_memory()
-        hk_np, hv_np, hq_np, ho_np = hk.numpy(), hv.numpy(), hq.numpy(), ho.numpy()
-        p2 = burr.default_params(partition_slots=P, min_partition_slots=a.min_partition_slots,
-                                 lower_partition_slots=a.lower_partition_slots, threshold_mode=tmode(a),
-                                 cut_search=cmode(a), cut_search_range=a.cut_search_range)
+        hk_np, hv_np = hk.numpy().view(np.uint64), hv.numpy()
+        p2 = params_for(0)
+        h = burr.build(hk_np, hv_np, r, params=p2)
+        ex_len = h.export_size()
+        h.free()
+        hx = torch.empty(ex_len, dtype=torch.uint8).pin_memory()
+        out_len = [0]
 
         def e2e_step():
             h = burr.build(hk_np, hv_np, r, params=p2)
-            h.query(hq_np, out=ho_np)
+            out_len[0] = h.export(out=hx)
             h.free()
 
         for _ in range(max(1, min(a.warmup, 2))):
             e2e_step()
-        assert np.array_equal(ho_np[:half], hv_np[:half])
         torch.cuda.synchronize()
         barrier(pg)
         t0 = time.perf_counter()
@@ -672,19 +745,46 @@ def main():
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / a.steps)
         line["e2e"] = {"value": ws * n / e2e_s / 1e6, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
-                       "h2d_bytes_per_step": n * 8 + n * vb + n * 8, "d2h_bytes_per_step": n * vb}
+                       "h2d_bytes_per_step": n * 8 + n * vb, "d2h_bytes_per_step": out_len[0],
+                       "step": "burr_build from page-locked host keys and values, burr_export of the "
+                               "structure into page-locked host memory, burr_free"}
+        del hk, hv, hx
 
     if not a.no_cpu and rank == 0:
+        cores, model = cpu_info()
         dt = oracle_sample(a.cpu_sample, r, P, a.min_partition_slots, a.lower_partition_slots, tmode(a),
-                      cmode(a), a.cut_search_range)
-        line["cpu_baseline"] = {"value": a.cpu_sample / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"serial C oracle: build + query of {a.cpu_sample} keys "
-                                          f"(same r, P, load; {dt:.1f} s)"}
+                           cmode(a), a.cut_search_range)
+        xor_steps = oracle_sample.xor_steps_per_row
+        dtm = oracle_sample(a.cpu_sample_mt, r, P, a.min_partition_slots, a.lower_partition_slots, tmode(a),
+                            cmode(a), a.cut_search_range, threads=cores)
+        line["cpu_baseline"] = {
+            "value": a.cpu_sample / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"serial C oracle: construction of {a.cpu_sample} keys of the same workload "
+                      f"(same r, P, load; {dt:.1f} s)",
+            "threaded": {"value": a.cpu_sample_mt / dtm / 1e6, "unit": UNIT, "cores": cores,
+                         "sample": f"the same oracle with each layer's partitions spread over {cores} host "
+                                   f"threads: construction of {a.cpu_sample_mt} keys ({dtm:.1f} s)"},
+            "nproc": cores, "cpu_model": model}
         # the dependent chain behind the band kernel's latency bound: row XORs
         # per insertion attempt of the serial elimination
-        line["breakdown"]["oracle_xor_steps_per_row"] = oracle_sample.xor_steps_per_row
+        line["breakdown"]["oracle_xor_steps_per_row"] = xor_steps
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    ws, rank, local, pg = dist_setup()
+    if a.impl == "reference":
+        run_reference(a, ws, rank, pg)
+        return
+    if a.workload == "batched":
+        run_batched(a, ws, rank, local, pg)
+        return
+    if a.workload == "serve":
+        run_served(a, ws, rank, local, pg)
+        return
+    run_plain(a, ws, rank, local, pg)
 
 
 if __name__ == "__main__":

@@ -227,12 +227,25 @@ class Handle:
         _check(load().burr_query(self._h, kp, op, n, st))
         return okeep
 
-    def export(self) -> bytes:
-        L = load()
+    def export_size(self) -> int:
+        """Bytes burr_export writes for this structure."""
         need = C.c_uint64(0)
-        L.burr_export(self._h, None, C.byref(need))
-        buf = (C.c_uint8 * need.value)()
-        ln = C.c_uint64(need.value)
+        load().burr_export(self._h, None, C.byref(need))
+        return need.value
+
+    def export(self, out=None):
+        """burr_export.  Without `out`: the export as bytes.  With `out` (a host
+        uint8 numpy array or CPU tensor, e.g. page-locked, of at least
+        export_size() bytes): written there; returns the bytes written."""
+        L = load()
+        if out is not None:
+            op, _, keep = _ptr_and_stream(out, None)
+            ln = C.c_uint64(int(keep.numel() if hasattr(keep, "numel") else keep.nbytes))
+            _check(L.burr_export(self._h, C.c_void_p(op), C.byref(ln)))
+            return ln.value
+        need = self.export_size()
+        buf = (C.c_uint8 * need)()
+        ln = C.c_uint64(need)
         _check(L.burr_export(self._h, buf, C.byref(ln)))
         return bytes(buf[:ln.value])
 

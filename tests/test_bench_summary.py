@@ -13,17 +13,18 @@ BAND = os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu")
 
 def test_committed_summary_matches_the_band_source():
     s = bench.ncu_band_summary(BAND)
-    assert s is not None, "profiles/k_band_1e8_r8_traffic.txt was taken on another band source"
-    assert s["dram_bytes"] > 1e9 and s["warp_instructions"] > 1e9
+    assert s is not None, "profiles/k_band_2e25_r8_traffic.txt was taken on another band source"
+    assert s["dram_bytes"] > 1e8 and s["warp_instructions"] > 1e9 and s["keys"] >= 1 << 20
 
 
 def test_summary_of_another_source_is_ignored(tmp_path):
     p = tmp_path / "summary.txt"
-    p.write_text("kernel_source_sha256_16: 0000000000000000\ndram_bytes_per_launch_scaled: 5\n")
+    p.write_text("kernel_source_sha256_16: 0000000000000000\ndram_bytes_per_launch_captured: 5\n"
+                 "n_keys_captured: 7\n")
     assert bench.ncu_band_summary(BAND, str(p)) is None
     h = hashlib.sha256(open(BAND, "rb").read()).hexdigest()[:16]
-    p.write_text(f"kernel_source_sha256_16: {h}\ndram_bytes_per_launch_scaled: 5\n")
-    assert bench.ncu_band_summary(BAND, str(p)) == {"dram_bytes": 5.0, "warp_instructions": None}
+    p.write_text(f"kernel_source_sha256_16: {h}\ndram_bytes_per_launch_captured: 5\nn_keys_captured: 7\n")
+    assert bench.ncu_band_summary(BAND, str(p)) == {"dram_bytes": 5.0, "warp_instructions": None, "keys": 7.0}
 
 
 def test_issue_roofline_arithmetic():
