@@ -89,6 +89,10 @@ extern "C" {
 #define BURR_CUT_DIFF 3u          /* cut search: least (bumped by the cut) - (keys before it) */
 #define BURR_MAX_LAYERS 8
 #define BURR_FLAG_TIMING 1u       /* record per-stage device times (burr_stats) */
+#define BURR_FLAG_TEST_WINDOW 2u  /* testing only: the band treats a pivot 136 or more slots past
+                                     its bucket's first slot as leaving the on-chip window (the
+                                     BURR_ERR_INTERNAL path of a real window overflow, which needs
+                                     a pivot 385 or more slots past its row's start) */
 
 typedef struct burr_handle burr_handle;
 

@@ -474,6 +474,11 @@ static void or_task_backsub(or_mt *M, unsigned tid)
         uint64_t s0 = q == 0 ? 0 : W->cuts[q - 1] + W->w;
         uint64_t s1 = q + 1 == M->K ? W->m : W->cuts[q] + W->w;
         if (s1 <= s0) continue;
+        if (M->prow[q] == M->prow[q + 1]) {
+            /* no rows: every slot it owns is free, so its table words are 0 */
+            memset(M->z + (s0 / 64) * W->r, 0, sizeof(uint64_t) * ((s1 - s0) / 64) * W->r);
+            continue;
+        }
         or_backsub_slots(M->W, s0, s1);
         or_pack_planes(W, s0, s1, M->z);
     }

@@ -19,6 +19,7 @@ BURR_OK = 0
 ERR_INVALID, ERR_OOM, ERR_UNSOLVABLE, ERR_TIMEOUT, ERR_CUDA, ERR_INTERNAL = -1, -2, -3, -4, -5, -6
 MAX_LAYERS = 8
 FLAG_TIMING = 1
+FLAG_TEST_WINDOW = 2
 THRESH_2BIT, THRESH_1PLUS = 0, 1
 CUT_NONE, CUT_MINBUMP, CUT_MAXPREV, CUT_DIFF = 0, 1, 2, 3
 

@@ -289,6 +289,10 @@ void free_layers(burr_handle *h) {
     }
 }
 
+// Window of the band under BURR_FLAG_TEST_WINDOW: small enough that ordinary
+// layers have pivots past it, so the overflow path can be driven by a test.
+constexpr uint32_t kTestWindow = 136;
+
 LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, uint64_t sigma, uint64_t K,
                     bool fallback, uint64_t P) {
     LayerDesc L;
@@ -307,6 +311,7 @@ LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, ui
     L.forced_code = (uint32_t)forced_code(p.levels);
     L.vmask = r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
     L.mode = p.threshold_mode;
+    L.window = (p.flags & BURR_FLAG_TEST_WINDOW) ? kTestWindow : 0u;
     return L;
 }
 

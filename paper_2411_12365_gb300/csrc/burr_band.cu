@@ -147,6 +147,12 @@ struct Ctx {
 
 enum { kOk = 0, kDependent = 1, kOverflow = 2 };
 
+// Pivots at or past bucket start + this many slots leave the live window (the
+// ring, unless a test asked for a smaller window).
+__device__ __forceinline__ uint32_t window_of(const LayerDesc &L) {
+    return L.window ? min(L.window, (uint32_t)kRing) : (uint32_t)kRing;
+}
+
 __device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int lane) {
     __syncwarp();
     for (uint32_t i = lane; i < ncommit; i += 32) {
@@ -263,7 +269,7 @@ __device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, 
 // and together they span all of the set's dependencies.  The result is then
 // kDependent if any row was dropped; a ring overflow still ends the set.
 template <int kLook, bool kTag = false>
-__device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, int lane) {
+__device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t bB, uint32_t wlim, int lane) {
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&S.ring[0]);
@@ -358,7 +364,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         }
         const uint32_t npos = pos + (uint32_t)tz;
         const bool dep = act && zero;
-        const bool ovf = act && !zero && npos - bB >= (uint32_t)kRing;
+        const bool ovf = act && !zero && npos - bB >= wlim;
         if (act) {
             cur = ((unsigned long long)n1 << 32) | n0;
             y = kTag ? ((unsigned long long)(yh | 1u) << 32) | y2 : kYValid | y2;
@@ -418,7 +424,7 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
             stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
-        const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, lane);
+        const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, window_of(x.L), lane);
         if (rc != kOk) {
             rollback(S, S.ncommit, lane);
             if (rc == kOverflow && lane == 0) atomicOr(a.err, kErrRingOverflow);
@@ -454,7 +460,7 @@ __device__ uint32_t insert_tagged(BandWarpSmem &S, const BandArgs<V> &a, const C
     if (lane == 0) S.ncommit = 0;
     __syncwarp();
     const uint32_t lo = S.first[forced];
-    const int rc = stream_insert<Lookahead<true>::value, true>(S, lo, S.first[x.L.B], bB, lane);
+    const int rc = stream_insert<Lookahead<true>::value, true>(S, lo, S.first[x.L.B], bB, window_of(x.L), lane);
     const uint32_t nc = S.ncommit;
     if (rc == kOk) {
         for (uint32_t i = lane; i < nc; i += 32) S.ring[S.clist[i]].y &= kYValid | 0xffffffffull;   // drop the tags

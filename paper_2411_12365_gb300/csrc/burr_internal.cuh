@@ -59,7 +59,7 @@ struct LayerDesc {
     uint32_t forced_code;
     uint32_t vmask;      // (1 << r) - 1
     uint32_t mode;       // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
-    uint32_t pad;
+    uint32_t window;     // pivots at or past bucket start + window leave the band's window (0 = the whole ring)
     const uint32_t *cuts;  // device: first bucket of each partition, [K] = nb; nullptr: partition j at j*P
 };
 

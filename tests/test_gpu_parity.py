@@ -166,49 +166,6 @@ def test_invalid_r():
             burr.build(keys, vals, r)
 
 
-def _owned(j, K, P, m):
-    return (0 if j == 0 else j * P + 64), (m if j == K - 1 else (j + 1) * P + 64)
-
-
-def test_full_size_1e8_sampled_partitions_and_invariants():
-    """n = 10^8, r = 8, P = 2^16 (the benchmark's launch configuration)."""
-    n, r, P = 100_000_000, 8, 65536
-    keys, vals = _kv(n, r)
-    h = burr.build(keys, vals, r, partition_slots=P, min_partition_slots=P)
-    st = h.stats()
-    # query(x) = f(x) for every key
-    assert torch.equal(h.query(keys), vals)
-    # negatives: fingerprint matches with probability 2^-r
-    neg = I.keys_torch(1 << 22, DEV, offset=n)
-    hits = int((h.query(neg) == I.values_torch(neg, r)).sum())
-    mean = (1 << 22) / 256.0
-    assert abs(hits - mean) < 6 * (mean ** 0.5)
-    # layer sizes follow the sizing rule
-    for l in range(4):
-        assert st["layer_m"][l] == O.layer_slots(st["layer_n"][l], 1.015)
-        if l < 3:
-            assert st["layer_n"][l + 1] == st["layer_bumped"][l]
-    # sampled layer-0 partitions rebuilt alone by the oracle (partitions are independent)
-    ex = parse(h.export())
-    L0 = ex["layers"][0]
-    m, K = L0["m"], L0["parts"]
-    assert K == O.num_partitions(m, P, P)
-    k_np = _u64(keys)
-    v_np = _vals_np(vals)
-    sigma = O.layer_seed(0x5EED5EED5EED5EED, 0)
-    starts, _ = O.hash_many(k_np, sigma, m)
-    cuts = [j * P for j in range(1, K)]
-    for j in (0, 1, K // 2, K - 1):
-        lo, hi = j * P, (m - 63 if j == K - 1 else (j + 1) * P)
-        sel = (starts >= lo) & (starts < hi)
-        res = O.build_layer(k_np[sel], v_np[sel], r, m, sigma, cuts=cuts)
-        a, b = _owned(j, K, P, m)
-        assert np.array_equal(res.z[(a // 64) * r:(b // 64) * r], L0["z"][(a // 64) * r:(b // 64) * r])
-        b0, b1 = lo // 128, (hi + 127) // 128
-        tw = lambda t, b: (int(t[b // 32]) >> (2 * (b % 32))) & 3  # noqa: E731
-        assert [tw(res.thresh, b) for b in range(b0, b1)] == [tw(L0["thresh"], b) for b in range(b0, b1)]
-
-
 # 1+-bit thresholds (Sec. 2): exact per-bucket thresholds, exports bit-equal
 
 ONEP_CASES = [
@@ -310,3 +267,16 @@ def test_64_slot_buckets_match_oracle(n, r, params):
     params = dict(params)
     params.setdefault("levels", (0, 16, 32, 64))
     _check_build(n, r, bucket_slots=64, **params)
+
+
+@pytest.mark.parametrize("mode", [burr.THRESH_2BIT, burr.THRESH_1PLUS])
+def test_band_window_overflow_is_an_error(mode):
+    """A pivot past the band's on-chip window is reported (BURR_ERR_INTERNAL),
+    never turned into a wrong table.  BURR_FLAG_TEST_WINDOW shrinks the window
+    to 136 slots past the bucket's first slot, which ordinary layers exceed, so
+    the path runs without a real overflow; the library stays usable after it."""
+    keys, vals = _kv(1 << 18, 8, seed=31)
+    with pytest.raises(burr.BurrError) as e:
+        burr.build(keys, vals, 8, threshold_mode=mode, flags=burr.FLAG_TEST_WINDOW)
+    assert e.value.code == burr.ERR_INTERNAL and "window" in str(e.value)
+    _check_build(1 << 18, 8, seed=31, threshold_mode=mode)
