@@ -335,6 +335,74 @@ int burr_stage_sort_noalloc(const uint64_t *d_keys, const void *d_values, uint64
                             void *stream);
 
 /*
+ * Sharded construction of ONE structure over several ranks (processes, GPUs,
+ * or shards sharing one GPU).  Paper: Sec. 3 ("Bumping" at thread
+ * boundaries): once a layer's cuts are placed, the first bucket after every
+ * cut bumps at least w-1 slots, so no kept equation crosses a cut and every
+ * partition is inserted and back-substituted independently.  Rank g owns the
+ * partitions [part_first[g], part_first[g+1]) of each bumping layer; a layer
+ * is built as:
+ *   1. n_layer = the layer's keys over all ranks (a sum the caller forms);
+ *   2. burr_shard_route: each rank groups its keys by owner rank (the owner of
+ *      the key's start bucket) -- the caller exchanges the groups (one
+ *      all-to-all of (key, value) records per layer);
+ *   3. burr_shard_build_layer: each rank sorts, bands and back-substitutes
+ *      its partitions; its bumped keys are its input of the next layer.
+ * After the last bumping layer one rank gathers the remaining keys and calls
+ * burr_shard_build_base.  The thresholds of the buckets each rank owns, its
+ * table words of the slots it owns ([c + 64, c' + 64) for its first cut c
+ * and the first cut c' after its range; from 0 for partition 0, to m for the
+ * last) and the base case together form the export of burr_build on the
+ * union of the keys, byte for byte (2-bit thresholds, cut j at j*P; cut search
+ * and 1+-bit thresholds are not supported here: BURR_ERR_INVALID).
+ * All key/value/table pointers are device memory owned by the caller.
+ */
+typedef struct {
+    uint64_t n;                 /* keys of the layer over all ranks */
+    uint64_t m;                 /* slots */
+    uint64_t buckets;
+    uint64_t partitions;        /* K: partition j starts at bucket j*P/B */
+    uint64_t partition_slots;   /* P */
+    uint64_t seed_index;        /* hash layer index (= the layer) */
+} burr_layer_geometry_t;
+
+/* Geometry of bumping layer `layer` (0 .. p->layers-1) holding n_layer keys:
+ * the sizing and partition rules of burr_build.  Host only. */
+int burr_layer_geometry(uint64_t n_layer, uint32_t layer, const burr_params *p, burr_layer_geometry_t *out);
+
+/* Group n (key, value) pairs by the rank that owns each key's start bucket in
+ * layer `layer` of n_layer keys.  part_first: host array of ranks+1 entries,
+ * from 0 to the layer's partitions, non-decreasing.  keys_out/values_out
+ * (n entries) receive rank 0's pairs, then rank 1's, ...; counts (host,
+ * ranks entries) their numbers.  The order inside a rank's run is not fixed.
+ * ranks <= 1024.  Returns after the output is written. */
+int burr_shard_route(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *p,
+                     uint32_t layer, uint64_t n_layer, uint32_t ranks, const uint32_t *part_first,
+                     uint64_t *keys_out, void *values_out, uint64_t *counts, void *stream);
+
+/* Build partitions [part_lo, part_hi) of layer `layer` (n_layer keys over all
+ * ranks) from their n keys -- exactly the keys whose start bucket lies in
+ * those partitions.  thresh: ceil(buckets/32) words, z: (m/64)*r words; both
+ * are cleared and then hold the codes of the range's buckets and the table
+ * words of the slots it owns.  bumped_keys/values (capacity n) receive the
+ * keys the range bumps, *nbumped (host) their number.  Returns after the
+ * results are written; BURR_ERR_INTERNAL if a device check tripped. */
+int burr_shard_build_layer(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *p,
+                           uint32_t layer, uint64_t n_layer, uint32_t part_lo, uint32_t part_hi, uint64_t *thresh,
+                           uint64_t *z, uint64_t *bumped_keys, void *bumped_values, uint64_t *nbumped,
+                           void *stream);
+
+/* The base case of n keys (all that the bumping layers bumped): no bumping,
+ * retried with the next seed and 10% more slots until it solves (Sec. 3,
+ * Sec. 4).  z must hold (m_max/64)*r words, m_max = the base-case slots of the
+ * last retry; with z NULL or smaller the call returns BURR_ERR_INVALID and
+ * sets *m_out = m_max.  Outputs: its slots, seed index (layers + attempt) and
+ * attempt.  BURR_ERR_UNSOLVABLE after the last retry (duplicate keys). */
+int burr_shard_build_base(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *p,
+                          uint64_t *z, uint64_t z_words, uint64_t *m_out, uint64_t *seed_index_out,
+                          uint32_t *attempt_out, void *stream);
+
+/*
  * Build/query server on one device: continuous batching of independent
  * builds with resident structures (the many-small-structures use of
  * retrieval, Sec. 1 "Applications"; the paper describes no server: the

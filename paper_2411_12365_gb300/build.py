@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", INCLUDE, "-I", CSRC]
 UNITS = ["burr_api.cu", "burr_sort.cu", "burr_band.cu", "burr_query.cu", "burr_noalloc.cu", "burr_server.cu",
-         "burr_thresh.cu", "burr_cuts.cu"]
+         "burr_thresh.cu", "burr_cuts.cu", "burr_shard.cu"]
 
 
 def _sources():

@@ -54,6 +54,10 @@ class Stats(C.Structure):
     ]
 
 
+class LayerGeometry(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("n", "m", "buckets", "partitions", "partition_slots", "seed_index")]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("memory_budget", C.c_uint64), ("host_staging_bytes", C.c_uint64),
                 ("max_batch_structures", C.c_uint32), ("pad", C.c_uint32)]
@@ -70,7 +74,8 @@ EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query
             "burr_stats", "burr_free", "burr_free_many", "burr_strerror", "burr_last_error", "burr_stage_hash",
             "burr_stage_sort", "burr_stage_sort_noalloc", "burr_server_create", "burr_server_submit_build",
             "burr_server_submit_query", "burr_server_wait", "burr_server_handle", "burr_server_release",
-            "burr_server_stats", "burr_server_destroy", "burr_set_allocator", "burr_import"]
+            "burr_server_stats", "burr_server_destroy", "burr_set_allocator", "burr_import",
+            "burr_layer_geometry", "burr_shard_route", "burr_shard_build_layer", "burr_shard_build_base"]
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -141,6 +146,17 @@ def load(path: str | None = None):
         L.burr_set_allocator.restype = i
         L.burr_import.argtypes = [p, u64, p, C.POINTER(p)]
         L.burr_import.restype = i
+        L.burr_layer_geometry.argtypes = [u64, u32, C.POINTER(Params), C.POINTER(LayerGeometry)]
+        L.burr_layer_geometry.restype = i
+        L.burr_shard_route.argtypes = [p, p, u64, u32, C.POINTER(Params), u32, u64, u32, C.POINTER(u32), p, p,
+                                       C.POINTER(u64), p]
+        L.burr_shard_route.restype = i
+        L.burr_shard_build_layer.argtypes = [p, p, u64, u32, C.POINTER(Params), u32, u64, u32, u32, p, p, p, p,
+                                             C.POINTER(u64), p]
+        L.burr_shard_build_layer.restype = i
+        L.burr_shard_build_base.argtypes = [p, p, u64, u32, C.POINTER(Params), p, u64, C.POINTER(u64),
+                                            C.POINTER(u64), C.POINTER(u32), p]
+        L.burr_shard_build_base.restype = i
         _lib = L
         return L
 
@@ -457,3 +473,68 @@ def use_torch_allocator(device=None):
     dev = torch.cuda.current_device() if device is None else device
     set_allocator(lambda n, stream: torch.cuda.caching_allocator_alloc(n, dev, stream),
                   lambda ptr, stream: torch.cuda.caching_allocator_delete(ptr))
+
+
+# --- sharded construction (burr_layer_geometry, burr_shard_*) ----------------
+
+def layer_geometry(n_layer: int, layer: int, params: Params | None = None, **kw) -> dict:
+    """burr_layer_geometry: slots, buckets and partitions of a bumping layer."""
+    if params is None:
+        params = default_params(**kw)
+    g = LayerGeometry()
+    _check(load().burr_layer_geometry(int(n_layer), int(layer), C.byref(params), C.byref(g)))
+    return {f: getattr(g, f) for f, _ in LayerGeometry._fields_}
+
+
+def shard_route(keys, values, r: int, layer: int, n_layer: int, part_first, params: Params, stream=None):
+    """burr_shard_route: (keys, values) grouped by owner rank, and the count of
+    each rank (CUDA tensors in, CUDA tensors and a list out)."""
+    import torch
+    ranks = len(part_first) - 1
+    n = keys.numel()
+    ko, vo = torch.empty_like(keys), torch.empty_like(values)
+    pf = (C.c_uint32 * (ranks + 1))(*[int(x) for x in part_first])
+    cnt = (C.c_uint64 * ranks)()
+    kp, st, _ = _ptr_and_stream(keys, _stream_value(stream))
+    _check(load().burr_shard_route(kp, values.data_ptr(), n, r, C.byref(params), layer, int(n_layer), ranks, pf,
+                                   ko.data_ptr(), vo.data_ptr(), cnt, st))
+    return ko, vo, [int(c) for c in cnt]
+
+
+def shard_build_layer(keys, values, r: int, layer: int, n_layer: int, part_lo: int, part_hi: int, params: Params,
+                      stream=None):
+    """burr_shard_build_layer: (threshold words, table words, bumped keys,
+    bumped values) of partitions [part_lo, part_hi), CUDA tensors."""
+    import torch
+    g = layer_geometry(n_layer, layer, params)
+    dev = keys.device
+    thresh = torch.empty(max((g["buckets"] + 31) // 32, 1), dtype=torch.int64, device=dev)
+    z = torch.empty(max((g["m"] // 64) * r, 1), dtype=torch.int64, device=dev)
+    n = keys.numel()
+    bk, bv = torch.empty(max(n, 1), dtype=keys.dtype, device=dev), torch.empty(max(n, 1), dtype=values.dtype,
+                                                                                 device=dev)
+    nb = C.c_uint64(0)
+    kp, st, _ = _ptr_and_stream(keys, _stream_value(stream))
+    _check(load().burr_shard_build_layer(kp, values.data_ptr(), n, r, C.byref(params), layer, int(n_layer),
+                                         int(part_lo), int(part_hi), thresh.data_ptr(), z.data_ptr(), bk.data_ptr(),
+                                         bv.data_ptr(), C.byref(nb), st))
+    k = nb.value
+    return (thresh[:(g["buckets"] + 31) // 32], z[:(g["m"] // 64) * r], bk[:k], bv[:k])
+
+
+def shard_build_base(keys, values, r: int, params: Params, stream=None):
+    """burr_shard_build_base: (table words, slots, seed index, attempt)."""
+    import torch
+    L = load()
+    n = keys.numel()
+    mo, so, ao = C.c_uint64(0), C.c_uint64(0), C.c_uint32(0)
+    kp, st, _ = _ptr_and_stream(keys, _stream_value(stream))
+    cap = 0
+    if n:   # ask for the largest table the retries may need
+        L.burr_shard_build_base(kp, values.data_ptr(), n, r, C.byref(params), None, 0, C.byref(mo), C.byref(so),
+                                C.byref(ao), st)
+        cap = (mo.value // 64) * r
+    z = torch.zeros(max(cap, 1), dtype=torch.int64, device=keys.device)
+    _check(L.burr_shard_build_base(kp, values.data_ptr(), n, r, C.byref(params), z.data_ptr(), cap,
+                                   C.byref(mo), C.byref(so), C.byref(ao), st))
+    return z[:(mo.value // 64) * r], mo.value, so.value, ao.value

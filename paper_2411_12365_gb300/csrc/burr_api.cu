@@ -1530,6 +1530,223 @@ const char *burr_strerror(int code) {
 
 const char *burr_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sharded construction (Sec. 3): the ranks of a build own contiguous ranges of
+// each layer's partitions.  A key goes to the rank that owns its start bucket
+// (burr_shard_route), each rank inserts and back-substitutes its partitions
+// alone (burr_shard_build_layer), the bumped keys are routed again for the
+// next layer, and one rank builds the base case (burr_shard_build_base).
+// ---------------------------------------------------------------------------
+namespace {
+
+// The layer that n_layer keys (all ranks) form as bumping layer `layer`: the
+// sizing, partition and seed rules of build_impl.
+LayerDesc shard_layer_desc(const burr_params &p, uint32_t r, uint64_t n_layer, uint32_t layer) {
+    const uint64_t m = layer_slots(n_layer, p.load_factor);
+    const uint64_t P = layer_partition_slots(p, layer);
+    return make_desc(p, r, n_layer, m, layer_seed(p.seed, layer), num_partitions(m, P, p.min_partition_slots), false,
+                     P);
+}
+
+int shard_params(const burr_params *pin, uint32_t r, burr_params &p) {
+    if (pin) p = *pin;
+    else burr_default_params(&p);
+    if (int rc = validate(p, r)) return rc;
+    if (p.threshold_mode != BURR_THRESH_2BIT)
+        return fail(BURR_ERR_INVALID, "sharded builds support 2-bit thresholds only");
+    if (p.cut_search != BURR_CUT_NONE)
+        return fail(BURR_ERR_INVALID, "sharded builds place cut j at j*P (no cut search)");
+    return BURR_OK;
+}
+
+int shard_layer_args(const burr_params &p, uint32_t r, uint32_t layer, uint64_t n, uint64_t n_layer, LayerDesc &L) {
+    if (layer >= p.layers) return fail(BURR_ERR_INVALID, "layer %u is not a bumping layer (layers = %u)", layer, p.layers);
+    if (n > n_layer) return fail(BURR_ERR_INVALID, "n = %llu exceeds the layer's n_layer", (unsigned long long)n);
+    if (n_layer >= (1ull << 32)) return fail(BURR_ERR_INVALID, "n_layer >= 2^32");
+    L = shard_layer_desc(p, r, n_layer, layer);
+    if (L.m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "layer needs >= 2^32 slots");
+    L.n = n;
+    return BURR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int burr_layer_geometry(uint64_t n_layer, uint32_t layer, const burr_params *pin, burr_layer_geometry_t *out) {
+    if (!out) return fail(BURR_ERR_INVALID, "out is NULL");
+    burr_params p;
+    if (int rc = shard_params(pin, 1, p)) return rc;
+    LayerDesc L;
+    if (int rc = shard_layer_args(p, 1, layer, 0, n_layer, L)) return rc;
+    out->n = n_layer;
+    out->m = L.m;
+    out->buckets = L.nb;
+    out->partitions = L.K;
+    out->partition_slots = L.P;
+    out->seed_index = layer;
+    return BURR_OK;
+}
+
+int burr_shard_route(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *pin,
+                     uint32_t layer, uint64_t n_layer, uint32_t ranks, const uint32_t *part_first, uint64_t *keys_out,
+                     void *values_out, uint64_t *counts, void *stream) {
+    burr_params p;
+    if (int rc = shard_params(pin, r, p)) return rc;
+    LayerDesc L;
+    if (int rc = shard_layer_args(p, r, layer, n, n_layer, L)) return rc;
+    if (!part_first || !counts) return fail(BURR_ERR_INVALID, "part_first/counts are NULL");
+    if (ranks == 0 || ranks > kMaxShardRanks) return fail(BURR_ERR_INVALID, "ranks must be in [1, %u]", kMaxShardRanks);
+    if (part_first[0] != 0 || part_first[ranks] != L.K)
+        return fail(BURR_ERR_INVALID, "part_first must run from 0 to the layer's %llu partitions",
+                    (unsigned long long)L.K);
+    for (uint32_t g = 0; g < ranks; ++g)
+        if (part_first[g] > part_first[g + 1]) return fail(BURR_ERR_INVALID, "part_first must not decrease");
+    for (uint32_t g = 0; g < ranks; ++g) counts[g] = 0;
+    if (n == 0) return BURR_OK;
+    if (!keys || !values || !keys_out || !values_out) return fail(BURR_ERR_INVALID, "NULL key/value pointer");
+    if (!is_device_ptr(keys) || !is_device_ptr(values) || !is_device_ptr(keys_out) || !is_device_ptr(values_out))
+        return fail(BURR_ERR_INVALID, "burr_shard_route takes device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t vb = value_bytes(r);
+    keep_pool_memory();
+    Arena ar(st);
+    uint32_t *d_pf, *rank_of;
+    unsigned long long *d_counts, *d_cursor;
+    CK(ar.alloc((void **)&d_pf, (ranks + 1) * 4ull), "alloc partition ranges");
+    CK(ar.alloc((void **)&rank_of, n * 4), "alloc owners");
+    CK(ar.alloc((void **)&d_counts, ranks * 8ull), "alloc counts");
+    CK(ar.alloc((void **)&d_cursor, ranks * 8ull), "alloc cursors");
+    CK(cudaMemcpyAsync(d_pf, part_first, (ranks + 1) * 4ull, cudaMemcpyHostToDevice, st), "copy partition ranges");
+    CK(cudaMemsetAsync(d_counts, 0, ranks * 8ull, st), "clear counts");
+    CK(launch_route(L, vb, keys, values, d_pf, ranks, rank_of, d_counts, nullptr, nullptr, nullptr, true, st), "route");
+    std::vector<unsigned long long> hc(ranks), cur(ranks);
+    CK(cudaMemcpyAsync(hc.data(), d_counts, ranks * 8ull, cudaMemcpyDeviceToHost, st), "read counts");
+    CK(cudaStreamSynchronize(st), "route counts");
+    unsigned long long run = 0;
+    for (uint32_t g = 0; g < ranks; ++g) {
+        cur[g] = run;
+        run += hc[g];
+        counts[g] = hc[g];
+    }
+    CK(cudaMemcpyAsync(d_cursor, cur.data(), ranks * 8ull, cudaMemcpyHostToDevice, st), "copy cursors");
+    CK(launch_route(L, vb, keys, values, d_pf, ranks, rank_of, nullptr, d_cursor, keys_out, values_out, false, st),
+       "route");
+    CK(cudaStreamSynchronize(st), "route");
+    return BURR_OK;
+}
+
+int burr_shard_build_layer(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *pin,
+                           uint32_t layer, uint64_t n_layer, uint32_t part_lo, uint32_t part_hi, uint64_t *thresh,
+                           uint64_t *z, uint64_t *bumped_keys, void *bumped_values, uint64_t *nbumped, void *stream) {
+    burr_params p;
+    if (int rc = shard_params(pin, r, p)) return rc;
+    LayerDesc L;
+    if (int rc = shard_layer_args(p, r, layer, n, n_layer, L)) return rc;
+    if (!nbumped) return fail(BURR_ERR_INVALID, "nbumped is NULL");
+    *nbumped = 0;
+    if (part_lo > part_hi || part_hi > L.K) return fail(BURR_ERR_INVALID, "partition range outside [0, K]");
+    if (n_layer == 0) return BURR_OK;
+    if (!thresh || !z || (n && (!keys || !values || !bumped_keys || !bumped_values)))
+        return fail(BURR_ERR_INVALID, "NULL pointer");
+    if (!is_device_ptr(thresh) || !is_device_ptr(z) ||
+        (n && (!is_device_ptr(keys) || !is_device_ptr(values) || !is_device_ptr(bumped_keys) ||
+               !is_device_ptr(bumped_values))))
+        return fail(BURR_ERR_INVALID, "burr_shard_build_layer takes device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t vb = value_bytes(r);
+    CK(cudaMemsetAsync(thresh, 0, ((L.nb + 31) / 32) * 8, st), "clear thresholds");
+    CK(cudaMemsetAsync(z, 0, (L.m / 64) * r * 8, st), "clear table");
+    if (part_lo == part_hi) return BURR_OK;
+    L.part_lo = part_lo;
+    L.part_hi = part_hi;
+    keep_pool_memory();
+    Arena ar(st);
+    void *sk, *sv, *bst, *ss, *cg, *yg, *ctr;
+    CK(ar.alloc(&sk, std::max<uint64_t>(n, 1) * 8), "alloc sorted keys");
+    CK(ar.alloc(&sv, std::max<uint64_t>(n, 1) * vb), "alloc sorted values");
+    CK(ar.alloc(&bst, (L.nb + 1) * 4), "alloc bucket offsets");
+    CK(ar.alloc(&ss, sort_scratch_bytes(n, L.m, vb)), "alloc sort scratch");
+    CK(ar.alloc(&cg, L.m * 8), "alloc band");
+    CK(ar.alloc(&yg, L.m * vb), "alloc band values");
+    CK(ar.alloc(&ctr, 64), "alloc counters");
+    CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
+    unsigned long long *bcount = (unsigned long long *)ctr;
+    uint32_t *err = (uint32_t *)((char *)ctr + 8);
+    CK(launch_sort(L, vb, keys, values, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+    CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, thresh, nullptr,
+                   bumped_keys, bumped_values, bcount, err, st),
+       "band");
+    CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, z, st), "backsub");
+    unsigned long long hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "shard layer");
+    const uint32_t e = (uint32_t)(hc[1] & 0xffffffffu);
+    if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band's window", layer);
+    if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", layer, e);
+    *nbumped = hc[0];
+    return BURR_OK;
+}
+
+int burr_shard_build_base(const uint64_t *keys, const void *values, uint64_t n, uint32_t r, const burr_params *pin,
+                          uint64_t *z, uint64_t z_words, uint64_t *m_out, uint64_t *seed_index_out,
+                          uint32_t *attempt_out, void *stream) {
+    burr_params p;
+    if (int rc = shard_params(pin, r, p)) return rc;
+    if (!m_out || !seed_index_out || !attempt_out) return fail(BURR_ERR_INVALID, "NULL output");
+    *m_out = 0;
+    *seed_index_out = p.layers;
+    *attempt_out = 0;
+    if (n == 0) return BURR_OK;
+    if (n >= (1ull << 32)) return fail(BURR_ERR_INVALID, "n >= 2^32");
+    const uint64_t need = (fallback_slots(n, p.fallback_slack, p.fallback_max_retries) / 64) * r;
+    if (!z || z_words < need) {
+        *m_out = fallback_slots(n, p.fallback_slack, p.fallback_max_retries);
+        return fail(BURR_ERR_INVALID, "z holds %llu words; the base case may need %llu", (unsigned long long)z_words,
+                    (unsigned long long)need);
+    }
+    if (!keys || !values || !is_device_ptr(keys) || !is_device_ptr(values) || !is_device_ptr(z))
+        return fail(BURR_ERR_INVALID, "burr_shard_build_base takes device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t vb = value_bytes(r);
+    keep_pool_memory();
+    Arena ar(st);
+    const uint64_t mmax = fallback_slots(n, p.fallback_slack, p.fallback_max_retries);
+    void *sk, *sv, *bst, *ss, *cg, *yg, *ctr;
+    CK(ar.alloc(&sk, n * 8), "alloc sorted keys");
+    CK(ar.alloc(&sv, n * vb), "alloc sorted values");
+    CK(ar.alloc(&bst, (num_buckets(mmax, p.bucket_slots) + 1) * 4), "alloc bucket offsets");
+    CK(ar.alloc(&ss, sort_scratch_bytes(n, mmax, vb)), "alloc sort scratch");
+    CK(ar.alloc(&cg, mmax * 8), "alloc band");
+    CK(ar.alloc(&yg, mmax * vb), "alloc band values");
+    CK(ar.alloc(&ctr, 64), "alloc counters");
+    uint32_t *err = (uint32_t *)((char *)ctr + 8);
+    for (uint32_t a = 0; a <= p.fallback_max_retries; ++a) {
+        const uint64_t m = fallback_slots(n, p.fallback_slack, a);
+        const LayerDesc L = make_desc(p, r, n, m, layer_seed(p.seed, p.layers + a), 1, true, m);
+        CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
+        CK(launch_sort(L, vb, keys, values, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+        CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, nullptr, nullptr,
+                       nullptr, nullptr, (unsigned long long *)ctr, err, st),
+           "band");
+        uint32_t he = 0;
+        CK(cudaMemcpyAsync(&he, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
+        CK(cudaStreamSynchronize(st), "base case");
+        if (he & ~kErrUnsolvable) return fail(BURR_ERR_INTERNAL, "base case: device error 0x%x", he);
+        if (he & kErrUnsolvable) continue;
+        CK(cudaMemsetAsync(z, 0, z_words * 8, st), "clear table");
+        CK(launch_backsub(L, vb, (const uint64_t *)cg, yg, z, st), "backsub");
+        CK(cudaStreamSynchronize(st), "base case");
+        *m_out = m;
+        *seed_index_out = p.layers + a;
+        *attempt_out = a;
+        return BURR_OK;
+    }
+    return fail(BURR_ERR_UNSOLVABLE, "base case unsolved after %u retries (duplicate keys?)", p.fallback_max_retries);
+}
+
 int burr_stage_hash(const uint64_t *d_keys, uint64_t n, uint64_t seed, uint32_t layer_index, uint64_t m,
                     uint32_t *d_start, uint64_t *d_coeff, void *stream) {
     if (m < kW || m % 64 || m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "m must be a multiple of 64 in [64, 2^32)");

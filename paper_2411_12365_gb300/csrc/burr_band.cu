@@ -588,7 +588,8 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
         x.bcount = a.bcount + si;
         x.fail = a.bv.fail ? a.bv.fail + si : nullptr;
     } else {
-        if (gp >= a.L.K) return;
+        gp += a.L.part_lo;
+        if (gp >= part_end(a.L)) return;
         x.L = a.L;
         x.part = gp;
         x.bucket_base = x.slot_base = x.tw_base = x.out_base = 0;
@@ -756,8 +757,8 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
     __shared__ uint32_t slen[kBsWarps][kBsGroups];   // its number of blocks
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = (uint32_t)lane / R, k = (uint32_t)lane % R;
-    uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q;
-    const uint64_t nparts = bv.sd ? bv.nparts : L0.K;
+    uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q + (bv.sd ? 0 : L0.part_lo);
+    const uint64_t nparts = bv.sd ? bv.nparts : part_end(L0);
     uint64_t bhi = 0, base = 0;
     uint32_t len = 0, r = 0;
     uint64_t *Z = Z0;
@@ -878,7 +879,7 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
     a.bvals = bvals;
     a.bcount = bcount;
     a.err = err;
-    const uint64_t parts = bv ? bv->nparts : L.K;
+    const uint64_t parts = bv ? bv->nparts : part_end(L) - L.part_lo;
     const unsigned grid = (unsigned)((parts + kBandWarps - 1) / kBandWarps);
     // the threshold mode is one for the whole launch (a batch shares its parameters)
     cudaError_t e;
@@ -898,7 +899,7 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
                         const uint32_t *bucket_start, uint64_t *Cg, void *Yg, uint64_t *thresh, uint8_t *texact,
                         uint64_t *bumped_keys, void *bumped_vals, unsigned long long *bumped_count,
                         uint32_t *err, cudaStream_t st, const BatchView *bv) {
-    if (bv ? bv->nparts == 0 : L.K == 0) return cudaSuccess;
+    if (bv ? bv->nparts == 0 : part_end(L) <= L.part_lo) return cudaSuccess;
     switch (vbytes) {
     case 1:
         return band_impl<uint8_t>(L, keys, (const uint8_t *)vals, bucket_start, Cg, (uint8_t *)Yg, thresh, texact,
@@ -914,7 +915,7 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
 
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
                            uint64_t *Z, cudaStream_t st, const BatchView *bv) {
-    const uint64_t parts = bv ? bv->nparts : L.K;
+    const uint64_t parts = bv ? bv->nparts : (part_end(L) > L.part_lo ? part_end(L) - L.part_lo : 0);
     if (parts == 0) return cudaSuccess;
     // several partitions per warp; a batch's structures may differ in r (up to 8 bits per value byte)
     const uint32_t R = bv ? 8u * vbytes : L.r;

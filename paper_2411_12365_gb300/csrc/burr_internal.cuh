@@ -60,8 +60,13 @@ struct LayerDesc {
     uint32_t vmask;      // (1 << r) - 1
     uint32_t mode;       // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
     uint32_t window;     // pivots at or past bucket start + window leave the band's window (0 = the whole ring)
+    uint32_t part_lo;    // band and back-substitution launches cover partitions [part_lo, part_hi)
+    uint32_t part_hi;    // (0: up to K); a shard of a sharded build owns such a range
     const uint32_t *cuts;  // device: first bucket of each partition, [K] = nb; nullptr: partition j at j*P
 };
+
+// End of the partition range a launch covers.
+__host__ __device__ inline uint64_t part_end(const LayerDesc &L) { return L.part_hi ? L.part_hi : L.K; }
 
 // First bucket of partition j (j <= K) and the slots it owns.
 __host__ __device__ inline uint64_t part_bucket(const LayerDesc &L, uint64_t j) {
@@ -207,6 +212,17 @@ cudaError_t launch_hash(const uint64_t *keys, uint64_t n, uint64_t sigma, uint64
 // Cut-point search (BURR_CUT_*): the first bucket of every partition of the
 // layer, cuts[0..K] (cuts[K] = nb), from the bucket-sorted keys.  With a
 // batch view, every structure's table sits at its L.cuts.
+// Sharded build: the owner rank of each of n keys in a layer (the rank whose
+// partition range [part_first[g], part_first[g+1]) holds the key's start
+// bucket; part_first has ranks+1 entries in device memory) and the keys and
+// values grouped by owner.  cursor: ranks device words holding each rank's
+// first output position, advanced by the call; rank_of: n words of scratch.
+constexpr uint32_t kMaxShardRanks = 1024;
+cudaError_t launch_route(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                         const uint32_t *part_first, uint32_t ranks, uint32_t *rank_of,
+                         unsigned long long *counts, unsigned long long *cursor, uint64_t *keys_out,
+                         void *vals_out, bool count_only, cudaStream_t st);
+
 cudaError_t launch_cut_search(const LayerDesc &L, const uint64_t *sorted_keys, const uint32_t *bucket_start,
                               uint32_t mode, uint32_t range, uint32_t *cuts, cudaStream_t st,
                               const BatchView *bv = nullptr);
