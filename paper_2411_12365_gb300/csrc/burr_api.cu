@@ -1771,7 +1771,7 @@ int burr_stage_sort(const uint64_t *d_keys, const void *d_values, uint64_t n, ui
     Arena ar(st);
     void *ss;
     CK(ar.alloc(&ss, sort_scratch_bytes(n, m, vb)), "alloc sort scratch");
-    CK(launch_sort(L, vb, d_keys, d_values, d_sorted_keys, d_sorted_values, d_bucket_start, ss, nullptr, st),
+    CK(launch_sort(L, vb, d_keys, d_values, d_sorted_keys, d_sorted_values, d_bucket_start, ss, nullptr, st, true),
        "sort");
     return BURR_OK;
 }

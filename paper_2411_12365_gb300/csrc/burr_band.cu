@@ -120,7 +120,7 @@ struct BandWarpSmem {
 template <typename V>
 struct BandArgs {
     LayerDesc L;
-    const uint64_t *keys;
+    const uint64_t *keys;    // bucket-sorted records h = mix64(key ^ sigma) of the layer's keys
     const V *vals;
     const uint32_t *bstart;
     uint64_t *Cg;
@@ -182,8 +182,9 @@ __device__ __noinline__ void stage_rows(BandWarpSmem &S, const BandArgs<V> &a, c
     for (int j = 0; j < kStagePerLane; ++j) {
         const uint32_t i = (uint32_t)lane + 32u * j;
         if (i < cnt) {
-            uint32_t s;
-            equation(a.keys[base + i], L.sigma, L.range, s, c[j]);
+            const uint64_t h = a.keys[base + i];     // the record h of the key
+            const uint32_t s = start_of_h(h, L.range);
+            c[j] = coeff_of_h(h, L.sigma);
             o[j] = s - bB;
             y[j] = (uint32_t)a.vals[base + i] & L.vmask;
             rank[j] = atomicAdd(&S.first[o[j]], 1u);
@@ -518,7 +519,8 @@ __device__ __forceinline__ uint32_t exact_threshold(BandWarpSmem &S, const BandA
     return t_ok;
 }
 
-// Rows of the bucket below threshold t leave for the next layer.
+// Rows of the bucket below threshold t leave for the next layer (as keys: the
+// next layer hashes them with its own seed).
 template <typename V>
 __device__ void emit_bumped(const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re, uint32_t bB,
                             uint32_t t, int lane) {
@@ -528,9 +530,12 @@ __device__ void emit_bumped(const BandArgs<V> &a, const Ctx &x, uint32_t rs, uin
         uint64_t key = 0;
         V val = 0;
         if (idx < re) {
-            key = a.keys[idx];
-            bump = (start_slot(key, x.L.sigma, x.L.range) - bB) < t;
-            if (bump) val = a.vals[idx];
+            const uint64_t h = a.keys[idx];
+            bump = (start_of_h(h, x.L.range) - bB) < t;
+            if (bump) {
+                key = key_of_h(h, x.L.sigma);
+                val = a.vals[idx];
+            }
         }
         const uint32_t mask = __ballot_sync(kFull, bump);
         if (!mask) continue;

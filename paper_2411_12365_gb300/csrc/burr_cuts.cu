@@ -24,7 +24,7 @@ __device__ __forceinline__ uint32_t count_offsets(const uint64_t *__restrict__ k
     uint32_t c = 0;
     const uint32_t e = bstart[g + 1];
     for (uint32_t i = bstart[g] + (uint32_t)lane; i < e; i += 32) {
-        const uint32_t o = start_slot(keys[i], L.sigma, L.range) - (uint32_t)(b * L.B);
+        const uint32_t o = start_of_h(keys[i], L.range) - (uint32_t)(b * L.B);   // keys[] holds records h
         c += (o >= lo && o < hi) ? 1u : 0u;
     }
     for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);

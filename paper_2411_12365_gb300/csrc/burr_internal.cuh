@@ -43,6 +43,43 @@ __device__ __forceinline__ void equation(uint64_t key, uint64_t sigma, uint64_t 
     coeff = mix64(h + sigma) | 1ull;
 }
 
+// The build's sorted records carry h = mix64(key ^ sigma), the first hash
+// round of the key in its layer, instead of the key: the later passes then
+// need one multiply-high for the start slot and one round for the
+// coefficients, and the key itself only where a row is bumped to the next
+// layer.  mix64 is a bijection (xor-shifts and multiplications by odd
+// constants), so h determines the key.
+__host__ __device__ __forceinline__ uint32_t start_of_h(uint64_t h, uint64_t range) {
+#ifdef __CUDA_ARCH__
+    return (uint32_t)__umul64hi(h, range);
+#else
+    return (uint32_t)(((unsigned __int128)h * range) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ uint64_t coeff_of_h(uint64_t h, uint64_t sigma) { return mix64(h + sigma) | 1ull; }
+
+// Inverse of an odd 64-bit multiplier modulo 2^64 (Newton's iteration
+// x <- x (2 - c x), which doubles the number of correct low bits; x = c is
+// right to 3 bits for odd c).
+__host__ __device__ constexpr uint64_t inverse_mod64(uint64_t c) {
+    uint64_t x = c;
+    for (int i = 0; i < 5; ++i) x *= 2 - c * x;
+    return x;
+}
+// Inverse of x ^= x >> s.
+__host__ __device__ __forceinline__ uint64_t unxorshift(uint64_t y, int s) {
+    uint64_t x = y;
+    for (int k = s; k < 64; k += s) x ^= y >> k;
+    return x;
+}
+// The key of record h in the layer with seed sigma: mix64 undone step by step.
+__host__ __device__ __forceinline__ uint64_t key_of_h(uint64_t h, uint64_t sigma) {
+    constexpr uint64_t i2 = inverse_mod64(0x94D049BB133111EBull), i1 = inverse_mod64(0xBF58476D1CE4E5B9ull);
+    uint64_t z = unxorshift(h, 31) * i2;
+    z = unxorshift(z, 27) * i1;
+    return unxorshift(z, 30) ^ sigma;
+}
+
 // One layer as the kernels see it.
 struct LayerDesc {
     uint64_t n;          // equations (keys) in the layer
@@ -114,11 +151,13 @@ size_t sort_scratch_bytes(uint64_t n, uint64_t m, uint32_t vbytes);
 // Kernels one launch_sort of this layer enqueues (n > 0).
 uint32_t sort_kernel_count(const LayerDesc &L);
 
-// Sort n (key, value) pairs of a layer into bucket order.
+// Sort n (key, value) pairs of a layer into bucket order.  The output holds
+// the records h = mix64(key ^ sigma) of the keys (what the band and the cut
+// search read), or the keys themselves with out_keys.
 // scratch: sort_scratch_bytes(n, m, vbytes) bytes of device memory.
 cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
-                        uint32_t *err, cudaStream_t st);
+                        uint32_t *err, cudaStream_t st, bool out_keys = false);
 
 // Band + bump (or base case), writing the band of every partition to Cg/Yg.
 // With a batch view (bv != nullptr) L is ignored: every partition of every
@@ -132,7 +171,8 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
                            uint64_t *Z, cudaStream_t st, const BatchView *bv = nullptr);
 
-// Batched sort: every structure's keys of the layer grouped by global bucket.
+// Batched sort: every structure's keys of the layer grouped by global bucket
+// (as records h of each structure's layer).
 size_t sort_batch_scratch_bytes(uint64_t nkeys, uint64_t ngroups, uint32_t vbytes);
 cudaError_t launch_sort_batch(const BatchView &bv, uint32_t vbytes, const uint64_t *keys, const void *vals,
                               uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,

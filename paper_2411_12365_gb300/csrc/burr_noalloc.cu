@@ -89,7 +89,7 @@ int burr_stage_sort_noalloc(const uint64_t *d_keys, const void *d_values, uint64
     // launch_sort zeroes the bin counters it accumulates into before use; every
     // other scratch word it reads was written earlier in the same call.
     cudaError_t e = launch_sort(L, vb, d_keys, d_values, d_sorted_keys, d_sorted_values, d_bucket_start, scratch,
-                                nullptr, (cudaStream_t)stream);
+                                nullptr, (cudaStream_t)stream, true);
     if (e != cudaSuccess) return set_error(BURR_ERR_CUDA, (std::string("sort: ") + cudaGetErrorString(e)).c_str());
     return BURR_OK;
 }

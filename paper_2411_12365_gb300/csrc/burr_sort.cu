@@ -15,8 +15,12 @@
 //   * the last pass sorts each group in shared memory (count, scan, place)
 //     and writes it out in order, together with the bucket offsets.
 //
-// The equation is recomputed from the key in every pass (the hash is fused
-// into its consumers) instead of materialising 16-byte records.
+// The first pass that writes turns each key into its record h = mix64(key ^
+// sigma), the first hash round of the key in the layer (8 bytes, like the
+// key, and a bijection of it).  Later passes and the band then find the start
+// slot with one multiply-high and the coefficients with one more round,
+// instead of hashing the key again in every pass; the band recovers the key
+// only for the rows it bumps.  The stage entry points ask for keys instead.
 #include <cstdio>
 
 #include "burr_internal.cuh"
@@ -90,8 +94,12 @@ Plan make_plan(const LayerDesc &L) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Sort group of a key (input of the first pass) and of a record h (later passes).
 __device__ __forceinline__ uint32_t group_of(uint64_t key, uint64_t sigma, uint64_t range, uint32_t gshift) {
     return start_slot(key, sigma, range) >> gshift;
+}
+__device__ __forceinline__ uint32_t group_of_h(uint64_t h, uint64_t range, uint32_t gshift) {
+    return start_of_h(h, range) >> gshift;
 }
 
 // counts[digit] of every key, digit = group >> dshift.
@@ -116,7 +124,8 @@ k_hist(const uint64_t *__restrict__ keys, uint64_t n, uint64_t sigma, uint64_t r
         if (sh[i]) atomicAdd(&counts[i], sh[i]);
 }
 
-// Per pass-1 bin (segment), counts of its low group bits: counts[group].
+// Per pass-1 bin (segment), counts of its low group bits: counts[group]
+// (from the records h the first pass wrote).
 __global__ void __launch_bounds__(kHistThreads)
 k_hist_seg(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ off1, uint32_t nseg_ctas,
            uint64_t sigma, uint64_t range, uint32_t gshift, uint32_t D2, uint32_t *__restrict__ counts) {
@@ -132,9 +141,9 @@ k_hist_seg(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ off1,
 #pragma unroll
         for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * stride];
 #pragma unroll
-        for (int j = 0; j < kUnroll; ++j) atomicAdd(&sh[group_of(k[j], sigma, range, gshift) & (D2 - 1)], 1u);
+        for (int j = 0; j < kUnroll; ++j) atomicAdd(&sh[group_of_h(k[j], range, gshift) & (D2 - 1)], 1u);
     }
-    for (; i < hi; i += stride) atomicAdd(&sh[group_of(keys[i], sigma, range, gshift) & (D2 - 1)], 1u);
+    for (; i < hi; i += stride) atomicAdd(&sh[group_of_h(keys[i], range, gshift) & (D2 - 1)], 1u);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < D2; i += blockDim.x)
         if (sh[i]) atomicAdd(&counts[(uint64_t)seg * D2 + i], sh[i]);
@@ -241,7 +250,10 @@ constexpr size_t scatter_smem_bytes() {
 // aligned-down address, when the array starts on 4 bytes and the rounded-up
 // end of the tile stays inside it; otherwise the tile's values are read
 // directly when it is worked on.
-template <typename V, bool SEG>
+//
+// RAW: the input holds keys, and the pass writes records h = mix64(key ^
+// sigma); otherwise the input already holds records.
+template <typename V, bool SEG, bool RAW>
 __global__ void __launch_bounds__(kTileThreads, 4)
 k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
           const uint32_t *__restrict__ off1, uint32_t nseg_ctas, uint64_t sigma, uint64_t range, uint32_t gshift,
@@ -307,7 +319,8 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
         for (int j = 0; j < kTileItems; ++j) {
             const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
             if (i < cnt) {
-                const uint32_t g = group_of(key[j], sigma, range, gshift);
+                if (RAW) key[j] = mix64(key[j] ^ sigma);
+                const uint32_t g = group_of_h(key[j], range, gshift);
                 dig[j] = SEG ? (g & (D - 1)) : (g >> dshift);
                 rank[j] = atomicAdd(&hist[dig[j]], 1u);
             }
@@ -355,7 +368,20 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
 // counted per bucket, placed into bucket order in shared memory and written
 // out contiguously; the bucket offsets are written too.  A group larger than
 // the shared-memory capacity is placed directly in global memory instead.
-template <typename V>
+// RAW: the input holds keys (a layer of one group, sorted in this pass
+// alone); otherwise records h.  OUT_KEYS: the output holds keys (the stage
+// entry points); otherwise records h (the build).
+template <bool RAW>
+__device__ __forceinline__ uint32_t bucket_in_group(uint64_t x, uint64_t sigma, uint64_t range, uint32_t log2B,
+                                                    uint64_t b_lo) {
+    return ((RAW ? start_slot(x, sigma, range) : start_of_h(x, range)) >> log2B) - (uint32_t)b_lo;
+}
+template <bool RAW, bool OUT_KEYS>
+__device__ __forceinline__ uint64_t group_out(uint64_t x, uint64_t sigma) {
+    if (RAW) return OUT_KEYS ? x : mix64(x ^ sigma);
+    return OUT_KEYS ? key_of_h(x, sigma) : x;
+}
+template <typename V, bool RAW, bool OUT_KEYS>
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, const uint32_t *__restrict__ goff,
              uint64_t sigma, uint64_t range, uint32_t log2B, uint64_t nb, uint64_t *__restrict__ keys_out,
@@ -378,10 +404,10 @@ k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, cons
             for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * blockDim.x];
 #pragma unroll
             for (int j = 0; j < kUnroll; ++j)
-                atomicAdd(&cnt[(start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+                atomicAdd(&cnt[bucket_in_group<RAW>(k[j], sigma, range, log2B, b_lo)], 1u);
         }
         for (; i < hi; i += blockDim.x)
-            atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+            atomicAdd(&cnt[bucket_in_group<RAW>(keys[i], sigma, range, log2B, b_lo)], 1u);
     }
     __syncthreads();
     block_scan(cnt, cur, kGroupBuckets, warp_sums);
@@ -400,17 +426,17 @@ k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, cons
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const uint32_t b = (start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo;
+                const uint32_t b = bucket_in_group<RAW>(k[j], sigma, range, log2B, b_lo);
                 const uint32_t p = atomicAdd(&cur[b], 1u);
-                skey[p] = k[j];
+                skey[p] = group_out<RAW, OUT_KEYS>(k[j], sigma);
                 sval[p] = v[j];
             }
         }
         for (; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
-            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t b = bucket_in_group<RAW>(key, sigma, range, log2B, b_lo);
             const uint32_t p = atomicAdd(&cur[b], 1u);
-            skey[p] = key;
+            skey[p] = group_out<RAW, OUT_KEYS>(key, sigma);
             sval[p] = vals[i];
         }
         __syncthreads();
@@ -421,9 +447,9 @@ k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, cons
     } else {
         for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
-            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t b = bucket_in_group<RAW>(key, sigma, range, log2B, b_lo);
             const uint32_t p = lo + atomicAdd(&cur[b], 1u);
-            keys_out[p] = key;
+            keys_out[p] = group_out<RAW, OUT_KEYS>(key, sigma);
             vals_out[p] = vals[i];
         }
     }
@@ -450,47 +476,58 @@ Scratch carve(void *scratch, uint64_t n, uint64_t ngroups, uint32_t vbytes) {
     return s;
 }
 
+// The group pass of sort_impl: RAW when it reads the caller's keys (a layer
+// of one group), OUT_KEYS when it writes keys instead of records.
+template <typename V, bool RAW, bool OUT_KEYS>
+cudaError_t launch_group_sort(const Plan &P, const LayerDesc &L, const uint64_t *gk, const V *gv, const uint32_t *goff,
+                              uint64_t *keys_out, V *vals_out, uint32_t *bucket_start, cudaStream_t st) {
+    const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
+    cudaError_t e = func_attr(k_group_sort<V, RAW, OUT_KEYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)group_smem);
+    if (e != cudaSuccess) return e;
+    if ((e = prefer_shared(k_group_sort<V, RAW, OUT_KEYS>)) != cudaSuccess) return e;
+    k_group_sort<V, RAW, OUT_KEYS><<<(unsigned)P.ngroups, kGroupThreads, group_smem, st>>>(
+        gk, gv, goff, L.sigma, L.range, P.log2B, L.nb, keys_out, vals_out, bucket_start);
+    return cudaGetLastError();
+}
+
 template <typename V>
 cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, uint64_t *keys_out, V *vals_out,
-                      uint32_t *bucket_start, void *scratch, cudaStream_t st) {
+                      uint32_t *bucket_start, void *scratch, bool out_keys, cudaStream_t st) {
     const uint64_t n = L.n;
     const Plan P = make_plan(L);
     Scratch S = carve(scratch, n, P.ngroups, sizeof(V));
     const unsigned sms = (unsigned)num_sms();
     const size_t tile_smem = scatter_smem_bytes<V>();
-    const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
     cudaError_t e;
-    e = func_attr(k_scatter<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+    e = func_attr(k_scatter<V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
     if (e != cudaSuccess) return e;
-    e = func_attr(k_scatter<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
-    if (e != cudaSuccess) return e;
-    e = func_attr(k_group_sort<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem);
+    e = func_attr(k_scatter<V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
     if (e != cudaSuccess) return e;
     if ((e = prefer_shared(k_hist)) != cudaSuccess || (e = prefer_shared(k_scan)) != cudaSuccess ||
-        (e = prefer_shared(k_scatter<V, false>)) != cudaSuccess || (e = prefer_shared(k_scatter<V, true>)) != cudaSuccess ||
-        (e = prefer_shared(k_hist_seg)) != cudaSuccess || (e = prefer_shared(k_group_sort<V>)) != cudaSuccess)
+        (e = prefer_shared(k_scatter<V, false, true>)) != cudaSuccess ||
+        (e = prefer_shared(k_scatter<V, true, false>)) != cudaSuccess || (e = prefer_shared(k_hist_seg)) != cudaSuccess)
         return e;
 
-    const uint32_t *goff;
-    const uint64_t *gk = keys;   // input of the group pass
-    const V *gv = vals;
     if (P.passes == 0) {
-        // one group: offsets [0, n]
+        // one group: offsets [0, n]; the group pass reads the keys themselves
         const uint32_t h[2] = {0, (uint32_t)n};
         e = cudaMemcpyAsync(S.o2, h, sizeof(h), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
-        goff = S.o2;
-    } else if (P.passes == 1) {
+        return out_keys ? launch_group_sort<V, true, true>(P, L, keys, vals, S.o2, keys_out, vals_out, bucket_start, st)
+                        : launch_group_sort<V, true, false>(P, L, keys, vals, S.o2, keys_out, vals_out, bucket_start,
+                                                            st);
+    }
+    const uint32_t *goff;
+    if (P.passes == 1) {
         e = cudaMemsetAsync(S.c1, 0, (size_t)P.D1 * 4, st);
         if (e != cudaSuccess) return e;
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, 0, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false, true><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, 0, P.D1, S.u1, S.keys, (V *)S.vals);
         goff = S.o1;
-        gk = S.keys;
-        gv = (const V *)S.vals;
     } else {
         // pass 1 into the caller's output buffers, pass 2 into scratch
         e = cudaMemsetAsync(S.c1, 0, (size_t)P.D1 * 4, st);
@@ -500,7 +537,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, P.d2, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false, true><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
         uint64_t per64 = (sms * 4ull + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
         if (per64 > 8) per64 = 8;
@@ -509,15 +546,16 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist_seg<<<P.D1 * per, kHistThreads, 0, st>>>(keys_out, S.o1, per, L.sigma, L.range, P.gshift, P.D2,
                                                          S.c2);
         k_scan<<<1, 1024, 0, st>>>(S.c2, (uint32_t)P.ngroups, S.o2, S.u2);
-        k_scatter<V, true><<<P.D1 * per, kTileThreads, tile_smem, st>>>(
+        k_scatter<V, true, false><<<P.D1 * per, kTileThreads, tile_smem, st>>>(
             keys_out, vals_out, n, S.o1, per, L.sigma, L.range, P.gshift, 0, P.D2, S.u2, S.keys, (V *)S.vals);
         goff = S.o2;
-        gk = S.keys;
-        gv = (const V *)S.vals;
     }
-    k_group_sort<V><<<(unsigned)P.ngroups, kGroupThreads, group_smem, st>>>(
-        gk, gv, goff, L.sigma, L.range, P.log2B, L.nb, keys_out, vals_out, bucket_start);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return out_keys ? launch_group_sort<V, false, true>(P, L, S.keys, (const V *)S.vals, goff, keys_out, vals_out,
+                                                        bucket_start, st)
+                    : launch_group_sort<V, false, false>(P, L, S.keys, (const V *)S.vals, goff, keys_out, vals_out,
+                                                         bucket_start, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -526,7 +564,8 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
 // numbered structure by structure, so grouping by global group keeps each
 // structure's keys contiguous and in bucket order.  One pass suffices per
 // structure (at most kMaxGroupsPerStruct groups each): tiles never straddle
-// structures (tile tables are built on the host).
+// structures (tile tables are built on the host).  The scatter turns each key
+// into its record h = mix64(key ^ sigma) of its structure's layer.
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kHistThreads)
@@ -571,7 +610,8 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
         if (i < cnt) {
             key[j] = keys[base + i];
             val[j] = vals[base + i];
-            dig[j] = group_of(key[j], D.L.sigma, D.L.range, gshift);
+            key[j] = mix64(key[j] ^ D.L.sigma);          // the record h of the key
+            dig[j] = group_of_h(key[j], D.L.range, gshift);
             rank[j] = atomicAdd(&hist[dig[j]], 1u);
         }
     }
@@ -598,8 +638,8 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
     }
 }
 
-// One block per global group: as k_group_sort, with the group's structure
-// looked up in the batch tables.
+// One block per global group: as k_group_sort (records h in and out), with
+// the group's structure looked up in the batch tables.
 template <typename V>
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, const uint32_t *__restrict__ goff,
@@ -626,10 +666,10 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
             for (int j = 0; j < kUnroll; ++j) k[j] = keys[i + j * blockDim.x];
 #pragma unroll
             for (int j = 0; j < kUnroll; ++j)
-                atomicAdd(&cnt[(start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+                atomicAdd(&cnt[(start_of_h(k[j], range) >> log2B) - (uint32_t)b_lo], 1u);
         }
         for (; i < hi; i += blockDim.x)
-            atomicAdd(&cnt[(start_slot(keys[i], sigma, range) >> log2B) - (uint32_t)b_lo], 1u);
+            atomicAdd(&cnt[(start_of_h(keys[i], range) >> log2B) - (uint32_t)b_lo], 1u);
     }
     __syncthreads();
     block_scan(cnt, cur, kGroupBuckets, warp_sums);
@@ -648,7 +688,7 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const uint32_t b = (start_slot(k[j], sigma, range) >> log2B) - (uint32_t)b_lo;
+                const uint32_t b = (start_of_h(k[j], range) >> log2B) - (uint32_t)b_lo;
                 const uint32_t p = atomicAdd(&cur[b], 1u);
                 skey[p] = k[j];
                 sval[p] = v[j];
@@ -656,7 +696,7 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
         }
         for (; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
-            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t b = (start_of_h(key, range) >> log2B) - (uint32_t)b_lo;
             const uint32_t p = atomicAdd(&cur[b], 1u);
             skey[p] = key;
             sval[p] = vals[i];
@@ -669,7 +709,7 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
     } else {
         for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const uint64_t key = keys[i];
-            const uint32_t b = (start_slot(key, sigma, range) >> log2B) - (uint32_t)b_lo;
+            const uint32_t b = (start_of_h(key, range) >> log2B) - (uint32_t)b_lo;
             const uint32_t p = lo + atomicAdd(&cur[b], 1u);
             keys_out[p] = key;
             vals_out[p] = vals[i];
@@ -742,15 +782,15 @@ uint32_t sort_kernel_count(const LayerDesc &L) {
 
 cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
-                        uint32_t * /*err*/, cudaStream_t st) {
+                        uint32_t * /*err*/, cudaStream_t st, bool out_keys) {
     if (L.n == 0) return cudaMemsetAsync(bucket_start, 0, (size_t)(L.nb + 1) * 4, st);
     switch (vbytes) {
     case 1: return sort_impl<uint8_t>(L, keys, (const uint8_t *)vals, keys_out, (uint8_t *)vals_out,
-                                      bucket_start, scratch, st);
+                                      bucket_start, scratch, out_keys, st);
     case 2: return sort_impl<uint16_t>(L, keys, (const uint16_t *)vals, keys_out, (uint16_t *)vals_out,
-                                       bucket_start, scratch, st);
+                                       bucket_start, scratch, out_keys, st);
     default: return sort_impl<uint32_t>(L, keys, (const uint32_t *)vals, keys_out, (uint32_t *)vals_out,
-                                        bucket_start, scratch, st);
+                                        bucket_start, scratch, out_keys, st);
     }
 }
 
