@@ -32,11 +32,31 @@ namespace {
 constexpr int kGroupShift = 6;                  // 64 buckets per group
 constexpr uint32_t kGroupBuckets = 1u << kGroupShift;
 constexpr int kHistThreads = 256;
-constexpr int kTileThreads = 256;
-constexpr int kTileItems = 8;
-constexpr int kTile = kTileThreads * kTileItems; // 2048 keys per tile (63 registers: 4 CTAs per SM)
+#ifndef BURR_SORT_TILE_THREADS
+#define BURR_SORT_TILE_THREADS 256
+#endif
+#ifndef BURR_SORT_TILE_ITEMS
+#define BURR_SORT_TILE_ITEMS 16
+#endif
+#ifndef BURR_SORT_TILE_CTAS
+#define BURR_SORT_TILE_CTAS 2
+#endif
+constexpr int kTileThreads = BURR_SORT_TILE_THREADS;
+constexpr int kTileItems = BURR_SORT_TILE_ITEMS;
+constexpr int kTileCtas = BURR_SORT_TILE_CTAS;     // CTAs per SM the scatter is compiled for
+// 4096 keys per tile, 2 CTAs per SM.  Longer tiles give longer runs per digit
+// and so fewer, fuller sectors per write: layer-0 sort of 10^9 keys (GB300)
+// 28.5 ms with 256 x 8 keys and 4 CTAs per SM, 24.8 with 256 x 16 and 2,
+// 24.7 with 256 x 20 and 2, 24.9 with 512 x 10 and 2, 25.2 with 512 x 16 and 1,
+// 27.8 with 256 x 12 and 3, 31.2 with 512 x 4 and 4.
+constexpr int kTile = kTileThreads * kTileItems;
 constexpr uint32_t kMaxDigits = 1024;           // digits of one scatter pass
-constexpr int kGroupThreads = 512;
+static_assert(kTile >= (int)kSortTile, "a batched sort tile must fit one scatter tile");
+static_assert(kMaxDigits % kTileThreads == 0, "the digit loops cover kMaxDigits in steps of the block");
+#ifndef BURR_GROUP_THREADS
+#define BURR_GROUP_THREADS 512
+#endif
+constexpr int kGroupThreads = BURR_GROUP_THREADS;
 constexpr uint32_t kGroupCap = 12288;           // keys a group may hold to be sorted in shared memory
 constexpr int kUnroll = 8;                      // keys in flight per thread in the counting loops
 
@@ -231,11 +251,11 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Shared memory of k_scatter: the ordered tile (keys, values, digits) and the
+// Shared memory of k_scatter: the ordered tile (records, values) and the
 // input buffer the next tile is copied into while this one is worked on.
 template <typename V>
 constexpr size_t scatter_smem_bytes() {
-    return (((size_t)kTile * (8 + sizeof(V) + 2) + 15) & ~(size_t)15) + (size_t)kTile * 8 + (size_t)kTile * sizeof(V) + 8;
+    return (((size_t)kTile * (8 + sizeof(V)) + 15) & ~(size_t)15) + (size_t)kTile * 8 + (size_t)kTile * sizeof(V) + 8;
 }
 
 // One scatter pass.  Tiles of kTile keys are ordered by digit in shared
@@ -254,7 +274,7 @@ constexpr size_t scatter_smem_bytes() {
 // RAW: the input holds keys, and the pass writes records h = mix64(key ^
 // sigma); otherwise the input already holds records.
 template <typename V, bool SEG, bool RAW>
-__global__ void __launch_bounds__(kTileThreads, 4)
+__global__ void __launch_bounds__(kTileThreads, kTileCtas)
 k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
           const uint32_t *__restrict__ off1, uint32_t nseg_ctas, uint64_t sigma, uint64_t range, uint32_t gshift,
           uint32_t dshift, uint32_t D, uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out,
@@ -262,8 +282,7 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
     V *sval = reinterpret_cast<V *>(skey + kTile);
-    uint16_t *sdig = reinterpret_cast<uint16_t *>(sval + kTile);
-    uint64_t *ikey = reinterpret_cast<uint64_t *>(smem_raw + (((size_t)kTile * (8 + sizeof(V) + 2) + 15) & ~(size_t)15));
+    uint64_t *ikey = reinterpret_cast<uint64_t *>(smem_raw + (((size_t)kTile * (8 + sizeof(V)) + 15) & ~(size_t)15));
     unsigned char *ival = reinterpret_cast<unsigned char *>(ikey + kTile);
     __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
 
@@ -347,14 +366,17 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
                 const uint32_t p = excl[dig[j]] + rank[j];
                 skey[p] = key[j];
                 sval[p] = val[j];
-                sdig[p] = (uint16_t)dig[j];
             }
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const uint32_t d = sdig[i];
+            // the digit again from the record (one multiply-high) instead of a
+            // third shared array written at random positions
+            const uint64_t h = skey[i];
+            const uint32_t g = group_of_h(h, range, gshift);
+            const uint32_t d = SEG ? (g & (D - 1)) : (g >> dshift);
             const uint32_t dst = gbase[d] + (i - excl[d]);
-            keys_out[dst] = skey[i];
+            keys_out[dst] = h;
             vals_out[dst] = sval[i];
         }
         __syncthreads();
@@ -525,7 +547,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, 0, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false, true><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false, true><<<grid_for(n, kTile, sms * kTileCtas), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, 0, P.D1, S.u1, S.keys, (V *)S.vals);
         goff = S.o1;
     } else {
@@ -537,9 +559,9 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_hist<<<grid_for(n, kHistThreads * 16, sms * 4), kHistThreads, 0, st>>>(keys, n, L.sigma, L.range,
                                                                                     P.gshift, P.d2, P.D1, S.c1);
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
-        k_scatter<V, false, true><<<grid_for(n, kTile, sms * 4), kTileThreads, tile_smem, st>>>(
+        k_scatter<V, false, true><<<grid_for(n, kTile, sms * kTileCtas), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
-        uint64_t per64 = (sms * 4ull + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
+        uint64_t per64 = (sms * (uint64_t)kTileCtas + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
         if (per64 > 8) per64 = 8;
         if (per64 < 1) per64 = 1;
         const uint32_t per = (uint32_t)per64;
@@ -592,7 +614,6 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
     V *sval = reinterpret_cast<V *>(skey + kTile);
-    uint16_t *sdig = reinterpret_cast<uint16_t *>(sval + kTile);
     __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
     const uint32_t t = blockIdx.x;
     const StructDesc &D = bv.sd[bv.tile_struct[t]];
@@ -626,12 +647,11 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
             const uint32_t p = excl[dig[j]] + rank[j];
             skey[p] = key[j];
             sval[p] = val[j];
-            sdig[p] = (uint16_t)dig[j];
         }
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint32_t d = sdig[i];
+        const uint32_t d = group_of_h(skey[i], D.L.range, gshift);   // skey holds records h
         const uint32_t dst = gbase[d] + (i - excl[d]);
         keys_out[dst] = skey[i];
         vals_out[dst] = sval[i];
@@ -728,7 +748,7 @@ cudaError_t sort_batch_impl(const BatchView &bv, const uint64_t *keys, const V *
     uint32_t *counts = (uint32_t *)p; p += align256(((uint64_t)bv.ngroups + 1) * 4);
     uint32_t *goff = (uint32_t *)p;   p += align256(((uint64_t)bv.ngroups + 1) * 4);
     uint32_t *cursor = (uint32_t *)p;
-    const size_t tile_smem = (size_t)kTile * (8 + sizeof(V) + 2);
+    const size_t tile_smem = (size_t)kTile * (8 + sizeof(V));
     const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
     cudaError_t e;
     e = func_attr(k_scatter_batch<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
