@@ -76,6 +76,9 @@ def args_():
                     help="serve: offered load points as fractions of the measured saturated capacity")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0, help="serve: admission budget")
     ap.add_argument("--serve-staging-gb", type=float, default=4.0, help="serve: page-locked payload region")
+    ap.add_argument("--serve-workers", type=int, default=1,
+                    help="serve: build workers (batches that overlap on the device); the other of 1 and 2 is also "
+                         "measured at 0.75 load")
     return ap.parse_args()
 
 
@@ -477,9 +480,12 @@ def run_served(a, ws, rank, local, pg):
     del kd
     torch.cuda.empty_cache()
     budget = int(a.serve_budget_gb * (1 << 30))
-    srv = burr.Server(budget, host_staging_bytes=int(a.serve_staging_gb * (1 << 30)),
-                      partition_slots=a.partition_slots, min_partition_slots=a.min_partition_slots,
-                      lower_partition_slots=a.lower_partition_slots, flags=burr.FLAG_TIMING)
+    def server(workers):
+        return burr.Server(budget, host_staging_bytes=int(a.serve_staging_gb * (1 << 30)), build_workers=workers,
+                           partition_slots=a.partition_slots, min_partition_slots=a.min_partition_slots,
+                           lower_partition_slots=a.lower_partition_slots, flags=burr.FLAG_TIMING)
+
+    srv = server(a.serve_workers)
     # warm-up (library load, pools, first launches), then saturated capacity
     ev, _ = serve_requests(max(8, a.serve_builds // 20), pool, seed=99)
     serve_run(srv, ev, keys, vals, None, 0)
@@ -492,7 +498,40 @@ def run_served(a, ws, rank, local, pg):
             r = serve_run(srv, events, keys, vals, f * cap_builds_s, 10 + i)
             r["load"] = f
             points.append(r)
+    # equal output: a sample of the stream's builds, served and built one call each
+    pp = burr.default_params(partition_slots=a.partition_slots, min_partition_slots=a.min_partition_slots,
+                             lower_partition_slots=a.lower_partition_slots)
+    sample = [e for e in events if e[0] == "build"][:12]
+    st = [srv.submit_build(keys[off:off + n], vals[off:off + n], 8) for _, n, off, _ in sample]
+    equal = True
+    for t, (_, n, off, _) in zip(st, sample):
+        srv.wait(t)
+        h = burr.build(keys[off:off + n], vals[off:off + n], 8, params=pp)
+        equal = equal and srv.handle(t).export() == h.export()
+        h.free()
+        srv.release(t)
     srv.close()
+    # the same build requests, one burr_build call each (host keys and values, as the server gets them)
+    builds = [e for e in events if e[0] == "build"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, n, off, _ in builds:
+        h = burr.build(keys[off:off + n], vals[off:off + n], 8, params=pp)
+        h.free()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain = {"builds": len(builds), "keys": int(sum(e[1] for e in builds)), "seconds": plain_s,
+             "mkeys_s": sum(e[1] for e in builds) / plain_s / 1e6,
+             "note": "the stream's build requests back to back, one burr_build call each, from host memory"}
+    # the other worker count (one: batches never overlap; two: a new batch starts while one runs)
+    # at the 0.75 load point, for the latency comparison
+    other_w = 2 if a.serve_workers == 1 else 1
+    s1 = server(other_w)
+    serve_run(s1, ev, keys, vals, None, 0)
+    other = serve_run(s1, events, keys, vals, 0.75 * cap_builds_s, 11)
+    other["load"] = 0.75
+    other["build_workers"] = other_w
+    s1.close()
     head = min(points, key=lambda r: abs(r["load"] - 0.75))
     value = max_over_ranks(pg, -head["served_mkeys_s"]) * -1 * ws if ws > 1 else head["served_mkeys_s"]
     if rank == 0:
@@ -510,7 +549,11 @@ def run_served(a, ws, rank, local, pg):
                        "l2_flush": "inputs larger than L2", "parallelism": "independent structures"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                     "note": "every request is host to device: this line is end to end"},
-            "serving": {"saturated": sat, "points": points},
+            "serving": {"build_workers": a.serve_workers, "saturated": sat, "points": points,
+                        "other_build_workers_at_0.75": other,
+                        "plain_one_call_per_build": plain,
+                        "served_saturated_over_plain": sat["served_mkeys_s"] / plain["mkeys_s"],
+                        "sample_exports_equal_served_vs_plain": equal},
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -618,6 +661,44 @@ def run_plain(a, ws, rank, local, pg):
             print(json.dumps({"ms_per_step": ms, "value": value}))
         return
 
+    # end to end through the C ABI (measured first, on a quiet pool): keys and values in page-locked host memory,
+    # the structure read back into page-locked host memory, copies inside the timed region
+    e2e_line = None
+    if not a.no_e2e:
+        hk = keys.cpu().pin_memory()
+        hv = vals.cpu().pin_memory()
+        hk_np, hv_np = hk.numpy().view(np.uint64), hv.numpy()
+        p2 = params_for(0)
+        h = burr.build(hk_np, hv_np, r, params=p2)
+        ex_len = h.export_size()
+        h.free()
+        hx = torch.empty(ex_len, dtype=torch.uint8).pin_memory()
+        out_len = [0]
+
+        def e2e_step():
+            h = burr.build(hk_np, hv_np, r, params=p2)
+            out_len[0] = h.export(out=hx)
+            h.free()
+
+        for _ in range(max(1, min(a.warmup, 2))):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        marks = []
+        for _ in range(a.steps):
+            e2e_step()
+            marks.append(time.perf_counter())
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / a.steps)
+        per = [1e3 * (b - a_) for a_, b in zip([t0] + marks[:-1], marks)]
+        e2e_line = {"value": ws * n / e2e_s / 1e6, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                    "step_ms_min_median_max": [min(per), statistics.median(per), max(per)],
+                    "h2d_bytes_per_step": n * 8 + n * vb, "d2h_bytes_per_step": out_len[0],
+                    "step": "burr_build from page-locked host keys and values, burr_export of the "
+                            "structure into page-locked host memory, burr_free"}
+        del hk, hv, hx
+
     st0 = stats_acc[-1]
     layers = st0["layers"]
     split = stage_split(stats_acc, layers)
@@ -693,6 +774,8 @@ def run_plain(a, ws, rank, local, pg):
         "gpu_launches": launches[0],
     }
     line["clocks"] = clk.summary()
+    if e2e_line:
+        line["e2e"] = e2e_line
     if summ and summ["warp_instructions"]:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = line["clocks"].get("sm_max_mhz") or 2070.0
@@ -716,39 +799,6 @@ def run_plain(a, ws, rank, local, pg):
             del v2
         line["breakdown"]["split_by_r"] = other
         torch.cuda.empty_cache()
-
-    # end to end through the C ABI: keys and values in page-locked host memory,
-    # the structure read back into page-locked host memory, copies inside the timed region
-    if not a.no_e2e:
-        hk = keys.cpu().pin_memory()
-        hv = vals.cpu().pin_memory()
-        hk_np, hv_np = hk.numpy().view(np.uint64), hv.numpy()
-        p2 = params_for(0)
-        h = burr.build(hk_np, hv_np, r, params=p2)
-        ex_len = h.export_size()
-        h.free()
-        hx = torch.empty(ex_len, dtype=torch.uint8).pin_memory()
-        out_len = [0]
-
-        def e2e_step():
-            h = burr.build(hk_np, hv_np, r, params=p2)
-            out_len[0] = h.export(out=hx)
-            h.free()
-
-        for _ in range(max(1, min(a.warmup, 2))):
-            e2e_step()
-        torch.cuda.synchronize()
-        barrier(pg)
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / a.steps)
-        line["e2e"] = {"value": ws * n / e2e_s / 1e6, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
-                       "h2d_bytes_per_step": n * 8 + n * vb, "d2h_bytes_per_step": out_len[0],
-                       "step": "burr_build from page-locked host keys and values, burr_export of the "
-                               "structure into page-locked host memory, burr_free"}
-        del hk, hv, hx
 
     if not a.no_cpu and rank == 0:
         cores, model = cpu_info()

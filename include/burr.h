@@ -408,11 +408,14 @@ int burr_shard_build_base(const uint64_t *keys, const void *values, uint64_t n, 
  * retrieval, Sec. 1 "Applications"; the paper describes no server: the
  * request loop is an interface of this library around burr_build_batch).
  *
- * A build worker thread repeatedly takes every queued build request whose
- * device-memory estimate fits the budget next to the resident structures and
- * the builds in flight, and builds them with one burr_build_batch call
- * per value width (structures larger than a batch allows get burr_build of
- * their own).  Requests submitted while a batch runs join the next one.
+ * Each of cfg.build_workers build worker threads (one stream each)
+ * repeatedly takes every queued build request whose device-memory estimate
+ * fits the budget next to the resident structures and the builds in flight,
+ * and builds them with one burr_build_batch call per value width (structures
+ * larger than a batch allows get burr_build of their own).  A request
+ * submitted while a batch runs is taken by an idle worker at once, so
+ * batches overlap on the device (continuous batching); with every worker
+ * busy it joins the next batch.
  * Payloads are copied at submission into a page-locked host region of
  * host_staging_bytes (so that the copies to the device are DMA at link
  * speed), or into pageable memory when the region has no room.  A query worker
@@ -428,7 +431,8 @@ typedef struct {
     uint64_t memory_budget;          /* device bytes for resident structures plus builds in flight (> 0) */
     uint64_t host_staging_bytes;     /* page-locked host region for request payloads (0 = none) */
     uint32_t max_batch_structures;   /* most structures per batch (0 = 4096) */
-    uint32_t pad;
+    uint32_t build_workers;          /* build worker threads, one stream each: batches that
+                                        overlap on the device (0 = 1, at most 8) */
 } burr_server_config;
 
 typedef struct {
@@ -442,8 +446,9 @@ typedef struct {
     uint64_t staged_requests;        /* payloads copied into the page-locked region */
     uint64_t pageable_requests;      /* payloads that did not fit it (pageable memory) */
     uint64_t built_keys;             /* keys of the builds completed or failed */
-    double build_busy_ms;            /* host time the build worker spent building */
+    double build_busy_ms;            /* host time the build workers spent building (summed) */
     double query_busy_ms;            /* host time the query worker spent querying */
+    uint64_t max_concurrent_batches; /* most admitted batches building at the same time */
 } burr_server_stats_t;
 
 /* Start a server on the current device.  p = NULL: defaults.  The server owns

@@ -60,14 +60,14 @@ class LayerGeometry(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("memory_budget", C.c_uint64), ("host_staging_bytes", C.c_uint64),
-                ("max_batch_structures", C.c_uint32), ("pad", C.c_uint32)]
+                ("max_batch_structures", C.c_uint32), ("build_workers", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("bytes_resident", "bytes_inflight", "resident_structures",
                                           "queued_builds", "queued_queries", "batches", "batched_structures",
                                           "staged_requests", "pageable_requests", "built_keys")] + [
-        ("build_busy_ms", C.c_double), ("query_busy_ms", C.c_double)]
+        ("build_busy_ms", C.c_double), ("query_busy_ms", C.c_double), ("max_concurrent_batches", C.c_uint64)]
 
 
 EXPORTED = ["burr_default_params", "burr_build", "burr_build_batch", "burr_query", "burr_size_bytes", "burr_export",
@@ -374,11 +374,11 @@ class Server:
     overlapping queries on one device (host keys, values and outputs)."""
 
     def __init__(self, memory_budget: int, params: Params | None = None, max_batch_structures: int = 0,
-                 host_staging_bytes: int = 1 << 30, **kw):
+                 host_staging_bytes: int = 1 << 30, build_workers: int = 0, **kw):
         if params is None:
             params = default_params(**kw)
         cfg = ServerConfig(memory_budget=int(memory_budget), host_staging_bytes=int(host_staging_bytes),
-                           max_batch_structures=int(max_batch_structures))
+                           max_batch_structures=int(max_batch_structures), build_workers=int(build_workers))
         out = C.c_void_p()
         _check(load().burr_server_create(C.byref(cfg), C.byref(params), C.byref(out)))
         self._s = out

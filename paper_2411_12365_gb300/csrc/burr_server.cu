@@ -1,14 +1,16 @@
 // burr_server.cu -- a build/query request server on one GPU (continuous
 // batching of the many-small-structures use of retrieval, Sec. 1).
 //
-// Two worker threads share the device:
-//   * the build worker takes every queued build request that the memory
-//     budget admits (its estimate fits next to the resident structures and
-//     the builds in flight) and builds them together: one burr_build_batch
-//     call per value width, inputs copied straight from each request's host
-//     buffer into the batch's device arrays; structures too large for a batch
-//     get burr_build of their own.  Requests that arrive while a batch is on
-//     the GPU wait and join the next batch;
+// Worker threads share the device:
+//   * each build worker (cfg.build_workers of them, one stream each) takes
+//     every queued build request that the memory budget admits (its estimate
+//     fits next to the resident structures and the builds in flight) and
+//     builds them together: one burr_build_batch call per value width, inputs
+//     copied straight from each request's host buffer into the batch's device
+//     arrays; structures too large for a batch get burr_build of their own.
+//     Requests that arrive while a batch is on the GPU are taken by an idle
+//     build worker at once, so batches overlap on the device; with every
+//     worker busy they join the next batch;
 //   * the query worker runs each query on its own stream as soon as the
 //     structure it targets is resident, overlapping the build worker's
 //     kernels.
@@ -142,10 +144,13 @@ struct burr_server {
     uint64_t running_query_target = 0;   // build ticket of the query in progress
     uint64_t batches = 0, batched_structures = 0, staged = 0, pageable = 0, built_keys = 0;
     double build_busy_ms = 0, query_busy_ms = 0;
+    uint64_t running_builds = 0, max_running_builds = 0;   // admitted batches on the device
     Staging staging;
     bool stop = false;
-    std::thread build_thread, query_thread;
-    cudaStream_t build_stream = nullptr, query_stream = nullptr;
+    std::vector<std::thread> build_threads;
+    std::thread query_thread;
+    std::vector<cudaStream_t> build_streams;
+    cudaStream_t query_stream = nullptr;
 };
 
 namespace {
@@ -200,9 +205,9 @@ std::vector<std::shared_ptr<Request>> admit(burr_server *S) {
     return batch;
 }
 
-int build_solo(burr_server *S, Request &q) {
+int build_solo(burr_server *S, Request &q, cudaStream_t st) {
     burr_handle *h = nullptr;
-    const int rc = burr_build(q.keys(), q.tail(), q.n, q.r, &S->params, S->build_stream, &h);
+    const int rc = burr_build(q.keys(), q.tail(), q.n, q.r, &S->params, st, &h);
     q.handle = rc == BURR_OK ? h : nullptr;
     if (rc) q.message = burr_last_error();
     return rc;
@@ -210,7 +215,7 @@ int build_solo(burr_server *S, Request &q) {
 
 // One burr_build_batch over requests of one value width: their payloads are
 // copied into the batch's device arrays, then built in one pass.
-int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
+int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb, cudaStream_t st) {
     std::vector<uint64_t> offs(g.size() + 1, 0);
     std::vector<uint32_t> rs(g.size());
     for (size_t j = 0; j < g.size(); ++j) {
@@ -218,7 +223,6 @@ int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
         rs[j] = g[j]->r;
     }
     const uint64_t N = offs.back();
-    cudaStream_t st = S->build_stream;
     uint64_t *dk = nullptr;
     uint8_t *dv = nullptr;
     if (N) {
@@ -252,7 +256,7 @@ int build_group(burr_server *S, std::vector<Request *> &g, uint32_t vb) {
 }
 
 // Build the requests of one admitted batch; returns per-request status.
-std::vector<int> build_all(burr_server *S, std::vector<std::shared_ptr<Request>> &batch) {
+std::vector<int> build_all(burr_server *S, std::vector<std::shared_ptr<Request>> &batch, cudaStream_t st) {
     std::vector<int> rc(batch.size(), BURR_OK);
     std::vector<Request *> groups[3];   // by value width 1, 2, 4 bytes
     std::vector<size_t> gidx[3];
@@ -265,26 +269,27 @@ std::vector<int> build_all(burr_server *S, std::vector<std::shared_ptr<Request>>
             groups[c].push_back(&q);
             gidx[c].push_back(i);
         } else {
-            rc[i] = build_solo(S, q);
+            rc[i] = build_solo(S, q, st);
         }
     }
     for (int c = 0; c < 3; ++c) {
         if (groups[c].empty()) continue;
-        if (build_group(S, groups[c], 1u << c) == BURR_OK) {
+        if (build_group(S, groups[c], 1u << c, st) == BURR_OK) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->batches += 1;
             S->batched_structures += groups[c].size();
         } else {
             // one failing structure fails the whole batch: build each on its
             // own so that only the failing request reports the error
-            for (size_t j = 0; j < groups[c].size(); ++j) rc[gidx[c][j]] = build_solo(S, *groups[c][j]);
+            for (size_t j = 0; j < groups[c].size(); ++j) rc[gidx[c][j]] = build_solo(S, *groups[c][j], st);
         }
     }
     return rc;
 }
 
-void build_worker(burr_server *S) {
+void build_worker(burr_server *S, size_t idx) {
     cudaSetDevice(S->device);
+    cudaStream_t st = S->build_streams[idx];
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         if (S->stop) {
@@ -300,11 +305,14 @@ void build_worker(burr_server *S) {
             S->cv_work.wait(lk);
             continue;
         }
+        S->running_builds += 1;
+        S->max_running_builds = std::max(S->max_running_builds, S->running_builds);
         lk.unlock();
         const auto t0 = Clock::now();
-        std::vector<int> rc = build_all(S, batch);
+        std::vector<int> rc = build_all(S, batch, st);
         const double busy = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
         lk.lock();
+        S->running_builds -= 1;
         S->build_busy_ms += busy;
         for (auto &q : batch) S->built_keys += q->n;
         for (size_t i = 0; i < batch.size(); ++i) {
@@ -385,15 +393,26 @@ int burr_server_create(const burr_server_config *cfg, const burr_params *p, burr
     S->cfg = *cfg;
     S->params = prm;
     if (S->cfg.max_batch_structures == 0) S->cfg.max_batch_structures = 4096;
+    if (S->cfg.build_workers == 0) S->cfg.build_workers = 1;
+    if (S->cfg.build_workers > 8) {
+        delete S;
+        return burr::set_error(BURR_ERR_INVALID, "build_workers must be at most 8");
+    }
     cudaGetDevice(&S->device);
-    if (cudaStreamCreateWithFlags(&S->build_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->query_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        if (S->build_stream) cudaStreamDestroy(S->build_stream);
+    bool ok = cudaStreamCreateWithFlags(&S->query_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (uint32_t i = 0; ok && i < S->cfg.build_workers; ++i) {
+        cudaStream_t b = nullptr;
+        ok = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) S->build_streams.push_back(b);
+    }
+    if (!ok) {
+        for (auto b : S->build_streams) cudaStreamDestroy(b);
+        if (S->query_stream) cudaStreamDestroy(S->query_stream);
         delete S;
         return burr::set_error(BURR_ERR_CUDA, "stream creation failed");
     }
     S->staging.init(cfg->host_staging_bytes);
-    S->build_thread = std::thread(build_worker, S);
+    for (size_t i = 0; i < S->build_streams.size(); ++i) S->build_threads.emplace_back(build_worker, S, i);
     S->query_thread = std::thread(query_worker, S);
     *out = S;
     return BURR_OK;
@@ -525,6 +544,7 @@ int burr_server_stats(burr_server *S, burr_server_stats_t *st) {
     st->built_keys = S->built_keys;
     st->build_busy_ms = S->build_busy_ms;
     st->query_busy_ms = S->query_busy_ms;
+    st->max_concurrent_batches = S->max_running_builds;
     for (auto &kv : S->reqs)
         if (kv.second->is_build && kv.second->status == 0) st->resident_structures += 1;
     return BURR_OK;
@@ -537,12 +557,13 @@ void burr_server_destroy(burr_server *S) {
         S->stop = true;
     }
     S->cv_work.notify_all();
-    if (S->build_thread.joinable()) S->build_thread.join();
+    for (auto &t : S->build_threads)
+        if (t.joinable()) t.join();
     S->cv_work.notify_all();
     if (S->query_thread.joinable()) S->query_thread.join();
     for (auto &kv : S->reqs)
         if (kv.second->is_build && kv.second->handle) burr_free(kv.second->handle);
-    cudaStreamDestroy(S->build_stream);
+    for (auto b : S->build_streams) cudaStreamDestroy(b);
     cudaStreamDestroy(S->query_stream);
     delete S;   // frees the staging region
 }

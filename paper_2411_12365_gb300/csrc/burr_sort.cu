@@ -561,8 +561,11 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
         k_scatter<V, false, true><<<grid_for(n, kTile, sms * kTileCtas), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
-        uint64_t per64 = (sms * (uint64_t)kTileCtas + P.D1 - 1) / P.D1;     // CTAs per pass-1 bin
-        if (per64 > 8) per64 = 8;
+        // CTAs per pass-1 bin: enough for about eight waves of the resident CTAs,
+        // so that the last wave leaves few SMs idle (with one CTA per bin and
+        // more bins than resident CTAs, the second wave ran half empty)
+        uint64_t per64 = (8ull * sms * (uint64_t)kTileCtas + P.D1 - 1) / P.D1;
+        if (per64 > 64) per64 = 64;
         if (per64 < 1) per64 = 1;
         const uint32_t per = (uint32_t)per64;
         k_hist_seg<<<P.D1 * per, kHistThreads, 0, st>>>(keys_out, S.o1, per, L.sigma, L.range, P.gshift, P.D2,

@@ -189,3 +189,33 @@ def test_server_1plus_thresholds():
             assert srv.handle(t).export() == _oracle(k, v, 8, threshold_mode=O.THRESH_1PLUS).export()
             out, _ = srv.wait(srv.submit_query(t, k))
             assert np.array_equal(out, v)
+
+
+@pytest.mark.parametrize("workers", [1, 3])
+def test_batches_overlap_and_equal_the_oracle(workers):
+    """Continuous batching: builds submitted while a batch is on the device are
+    taken by an idle build worker at once (their own stream), so batches
+    overlap; every structure still equals the oracle's for its keys."""
+    big = _request(40, 3_000_000, 8)
+    small = [_request(41 + i, int(n), 8) for i, n in enumerate([5000, 70_000, 1, 0, 20_000, 150_000])]
+    with burr.Server(16 << 30, build_workers=workers, **PARAMS) as srv:
+        tb = srv.submit_build(*big, 8)
+        for _ in range(2000):                      # the big build is admitted and running
+            st = srv.stats()
+            if st["queued_builds"] == 0 and st["bytes_inflight"] > 0:
+                break
+            time.sleep(0.001)
+        ts = [srv.submit_build(k, v, 8) for k, v in small]
+        for t in [tb] + ts:
+            srv.wait(t)
+        st = srv.stats()
+        if workers == 1:
+            assert st["max_concurrent_batches"] == 1
+        else:
+            assert st["max_concurrent_batches"] >= 2
+        for t, (k, v) in zip(ts, small):
+            got, want = srv.handle(t).export(), _oracle(k, v, 8).export()
+            assert got == want, describe_difference(got, want)
+        sel = np.random.default_rng(1).choice(len(big[0]), 100_000, replace=False)
+        out, _ = srv.wait(srv.submit_query(tb, big[0][sel]))
+        assert np.array_equal(out, big[1][sel])
