@@ -3,6 +3,7 @@ that include/burr.h declares (host-only calls; no GPU needed)."""
 import ctypes as C
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -69,7 +70,20 @@ def test_server_rejects_bad_config_without_touching_the_device(lib):
         with pytest.raises(burr.BurrError) as e:
             burr.Server(budget, **kw)
         assert e.value.code == burr.ERR_INVALID
-    assert C.sizeof(burr.ServerConfig) == 24 and C.sizeof(burr.ServerStats) == 96
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures have the sizes the C compiler gives the header's."""
+    from paper_2411_12365_gb300 import burr
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "burr.h"\nint main(void) { printf("%zu %zu %zu %zu %zu\\n", '
+                   "sizeof(burr_params), sizeof(burr_stats_t), sizeof(burr_server_config), "
+                   "sizeof(burr_server_stats_t), sizeof(burr_layer_geometry_t)); return 0; }\n")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [C.sizeof(burr.Params), C.sizeof(burr.Stats), C.sizeof(burr.ServerConfig),
+                   C.sizeof(burr.ServerStats), C.sizeof(burr.LayerGeometry)]
 
 
 def test_allocator_hook_arguments_without_the_device(lib):
