@@ -169,38 +169,60 @@ k_hist_seg(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ off1,
         if (sh[i]) atomicAdd(&counts[(uint64_t)seg * D2 + i], sh[i]);
 }
 
-// Exclusive scan of counts[0..len) into off[0..len] and cursor[0..len), one block.
+// Exclusive scan of counts[0..len) into off[0..len] and cursor[0..len), one
+// block.  The counts go through shared memory in tiles of kScanItems * 1024
+// (coalesced loads, every thread then scans kScanItems consecutive entries),
+// with the running total carried from tile to tile: the 120k group counts of a
+// 10^9-key layer took 0.44 ms when each thread walked its own 117 entries in
+// global memory.
+constexpr int kScanItems = 8;
 __global__ void __launch_bounds__(1024)
 k_scan(const uint32_t *__restrict__ counts, uint32_t len, uint32_t *__restrict__ off, uint32_t *__restrict__ cursor) {
+    __shared__ uint32_t tile[kScanItems * 1024];
     __shared__ uint32_t warp_sums[32];
-    const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = threadIdx.x * per;
-    uint32_t local = 0;
-    for (uint32_t i = lo; i < lo + per && i < len; ++i) local += counts[i];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = local;
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-            if (lane >= d) s += y;
+    const uint32_t T = (uint32_t)kScanItems * blockDim.x;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < len; base += T) {
+        const uint32_t n = min(T, len - base);
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) tile[i] = counts[base + i];
+        __syncthreads();
+        const uint32_t lo = threadIdx.x * kScanItems;
+        uint32_t v[kScanItems], local = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            v[k] = lo + k < n ? tile[lo + k] : 0u;
+            local += v[k];
         }
-        warp_sums[lane] = s;
+        uint32_t x = local;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        uint32_t run = carry + x - local + (warp ? warp_sums[warp - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (lo + k < n) {
+                off[base + lo + k] = run;
+                cursor[base + lo + k] = run;
+            }
+            run += v[k];
+        }
+        carry += warp_sums[(blockDim.x >> 5) - 1];
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = x - local + (warp ? warp_sums[warp - 1] : 0);
-    for (uint32_t i = lo; i < lo + per && i < len; ++i) {
-        off[i] = run;
-        cursor[i] = run;
-        run += counts[i];
-    }
-    if (threadIdx.x == blockDim.x - 1) off[len] = run;
+    if (threadIdx.x == 0) off[len] = carry;
 }
 
 // Block-wide exclusive scan of cnt[0..len) (len <= kMaxDigits) into out[].
