@@ -349,6 +349,12 @@ struct Timer {
 // the side stream, so every later free on the build stream is ordered after
 // the side stream's reads.
 constexpr int kBandSets = 3;
+// CTAs per SM of a bumping layer's back-substitution (0: no cap).  It runs
+// beside the next layers; capped, it leaves registers free for their kernels.
+#ifndef BURR_BACKSUB_CTAS_PER_SM
+#define BURR_BACKSUB_CTAS_PER_SM 0
+#endif
+constexpr uint32_t kBacksubCtasPerSm = BURR_BACKSUB_CTAS_PER_SM;
 constexpr int kOrderSlot = kBandSets;      // event slots after the per-set ones
 constexpr int kJoinSlot = kBandSets + 1;
 constexpr int kFinalSlot = kBandSets + 2;
@@ -447,6 +453,29 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         CK(cudaMemsetAsync(blkseg, 0, dir_blocks(cap_nb) * 4, st), "clear threshold blocks");
     }
 
+    // A bumping layer's back-substitution is queued on the side stream only
+    // after the next layer's sort: it fills every SM for milliseconds, and the
+    // sort, queued behind it, used to wait that long (layer 1 of a 10^9-key
+    // build started 2.9 ms after layer 0's band ended).
+    struct PendingBacksub {
+        bool on;
+        uint32_t l;
+        int set;
+        LayerDesc L;
+        uint64_t *z;
+    } pending{};
+    auto start_backsub = [&]() -> cudaError_t {
+        if (!pending.on) return cudaSuccess;
+        pending.on = false;
+        cudaError_t e = side.order(st, side.side, kOrderSlot);
+        if (e != cudaSuccess) return e;
+        tev[pending.l][3] = tm.mark_on(side.side);
+        e = launch_backsub(pending.L, vb, (const uint64_t *)cgs[pending.set], ygs[pending.set], pending.z, side.side,
+                           nullptr, kBacksubCtasPerSm);
+        if (e != cudaSuccess) return e;
+        tev[pending.l][4] = tm.mark_on(side.side);
+        return side.solved(pending.set);
+    };
     const uint64_t *cur_k = dkeys;
     const void *cur_v = dvals;
     uint64_t cur_n = n;
@@ -498,6 +527,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         CK(side.reuse(set), "order");
         tev[l][0] = tm.mark();
         CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+        CK(start_backsub(), "backsub");   // the previous layer's, now that this layer's sort is queued
         if (search) {
             CK(launch_cut_search(L, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search, p.cut_search_range,
                                  const_cast<uint32_t *>(L.cuts), st),
@@ -509,11 +539,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
                        S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
         tev[l][2] = tm.mark();
         if (onep) CK(launch_thresh_flags(tex, dseg, blkseg, (uint32_t)nd, S.flags, tcounts, S.dir, st), "flags");
-        CK(side.order(st, side.side, kOrderSlot), "order");
-        tev[l][3] = tm.mark_on(side.side);
-        CK(launch_backsub(L, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side), "backsub");
-        tev[l][4] = tm.mark_on(side.side);
-        CK(side.solved(set), "order");
+        pending = PendingBacksub{true, l, set, L, S.z};
         h->launches += sort_kernel_count(L) + 2 + (onep ? 2 : 0);
         unsigned long long hc[2] = {0, 0};
         uint32_t nflag = 0;
@@ -539,6 +565,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         which ^= 1;   // layer l+1 reads this list and bumps into the other one (n_{l+1} <= n_l)
     }
 
+    CK(start_backsub(), "backsub");   // the last bumping layer's
     // base case: no bumping; grow by 10% and change the seed until it solves
     LayerStore &F = h->L[p.layers];
     F.n = cur_n;

@@ -751,18 +751,26 @@ __device__ __forceinline__ uint32_t parity64(uint64_t x) {
 // group idles until the longest one is done.
 constexpr int kBsGroups = 8;
 
-template <typename V>
-__global__ void __launch_bounds__(32 * kBsWarps)
+//
+// kG (1, 2, 4 or 8) bounds G at compile time, so that the per-group registers
+// of a launch with few groups (G = 4 at r = 8) are not those of eight.  A warp
+// job is one set of G partitions; the grid may hold fewer warps than jobs
+// (a cap on the CTAs per SM leaves room beside it for the next layer's
+// kernels), and then every warp walks the jobs with the grid's stride.
+template <typename V, int kG>
+__global__ void __launch_bounds__(32 * kBsWarps, kG >= 8 ? 4 : 1)
 k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z0,
-                BatchView bv, uint32_t R, uint32_t G) {
-    __shared__ uint64_t sc[kBsWarps][kBsGroups][64];
-    __shared__ uint32_t sy[kBsWarps][kBsGroups][64];
-    __shared__ uint64_t sbase[kBsWarps][kBsGroups];  // first slot of the group's structure in the layer arrays
-    __shared__ uint64_t shi[kBsWarps][kBsGroups];    // one past the last block of the group's partition
-    __shared__ uint32_t slen[kBsWarps][kBsGroups];   // its number of blocks
+                BatchView bv, uint32_t R, uint32_t G, uint64_t njobs) {
+    __shared__ uint64_t sc[kBsWarps][kG][64];
+    __shared__ uint32_t sy[kBsWarps][kG][64];
+    __shared__ uint64_t sbase[kBsWarps][kG];  // first slot of the group's structure in the layer arrays
+    __shared__ uint64_t shi[kBsWarps][kG];    // one past the last block of the group's partition
+    __shared__ uint32_t slen[kBsWarps][kG];   // its number of blocks
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t q = (uint32_t)lane / R, k = (uint32_t)lane % R;
-    uint64_t gp = ((uint64_t)blockIdx.x * kBsWarps + warp) * G + q + (bv.sd ? 0 : L0.part_lo);
+    for (uint64_t job = (uint64_t)blockIdx.x * kBsWarps + warp; job < njobs;
+         job += (uint64_t)gridDim.x * kBsWarps) {
+    uint64_t gp = job * G + q + (bv.sd ? 0 : L0.part_lo);
     const uint64_t nparts = bv.sd ? bv.nparts : part_end(L0);
     uint64_t bhi = 0, base = 0;
     uint32_t len = 0, r = 0;
@@ -795,20 +803,20 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
     }
     const uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
     __syncwarp();
-    if (maxlen == 0) return;
-    uint64_t gh[kBsGroups], gb[kBsGroups];
-    uint32_t gl[kBsGroups];
+    if (maxlen == 0) continue;
+    uint64_t gh[kG], gb[kG];
+    uint32_t gl[kG];
 #pragma unroll
-    for (int g = 0; g < kBsGroups; ++g) {
+    for (int g = 0; g < kG; ++g) {
         gh[g] = (uint32_t)g < G ? shi[warp][g] : 0;
         gb[g] = (uint32_t)g < G ? sbase[warp][g] : 0;
         gl[g] = (uint32_t)g < G ? slen[warp][g] : 0;
     }
     // software pipeline: registers hold every group's next block while this one is solved
-    uint64_t nc0[kBsGroups], nc1[kBsGroups];
-    uint32_t ny0[kBsGroups], ny1[kBsGroups];
+    uint64_t nc0[kG], nc1[kG];
+    uint32_t ny0[kG], ny1[kG];
 #pragma unroll
-    for (int g = 0; g < kBsGroups; ++g) {
+    for (int g = 0; g < kG; ++g) {
         nc0[g] = nc1[g] = 0;
         ny0[g] = ny1[g] = 0;
         if (gl[g] > 0) {
@@ -824,7 +832,7 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
     for (uint32_t t = 0; t < maxlen; ++t) {
         __syncwarp();
 #pragma unroll
-        for (int g = 0; g < kBsGroups; ++g) {
+        for (int g = 0; g < kG; ++g) {
             if (t < gl[g]) {
                 sc[warp][g][lane] = nc0[g] >> 1;
                 sc[warp][g][lane + 32] = nc1[g] >> 1;
@@ -834,7 +842,7 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
         }
         __syncwarp();
 #pragma unroll
-        for (int g = 0; g < kBsGroups; ++g) {
+        for (int g = 0; g < kG; ++g) {
             if (t + 1 < gl[g]) {
                 const uint64_t s0 = gb[g] + ((gh[g] - 2 - t) << 6);
                 nc0[g] = Cg[s0 + lane];
@@ -863,6 +871,8 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
             }
             Z[(bhi - 1 - t) * r + k] = T;
         }
+    }
+    __syncwarp();   // the warp's shared arrays are reused by its next job
     }
 }
 
@@ -918,26 +928,45 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
     }
 }
 
+template <typename V, int kG>
+cudaError_t backsub_launch(const LayerDesc &L, const uint64_t *Cg, const V *Yg, uint64_t *Z, cudaStream_t st,
+                           const BatchView &v, uint32_t R, uint32_t G, uint64_t njobs, unsigned grid) {
+    const cudaError_t e = prefer_shared(k_backsub_multi<V, kG>);
+    if (e != cudaSuccess) return e;
+    k_backsub_multi<V, kG><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, Yg, Z, v, R, G, njobs);
+    return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t backsub_impl(const LayerDesc &L, const uint64_t *Cg, const V *Yg, uint64_t *Z, cudaStream_t st,
+                         const BatchView &v, uint32_t R, uint32_t G, uint64_t njobs, unsigned grid) {
+    if (G <= 1) return backsub_launch<V, 1>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    if (G <= 2) return backsub_launch<V, 2>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    if (G <= 4) return backsub_launch<V, 4>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    return backsub_launch<V, kBsGroups>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+}
+
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
-                           uint64_t *Z, cudaStream_t st, const BatchView *bv) {
+                           uint64_t *Z, cudaStream_t st, const BatchView *bv, uint32_t max_ctas_per_sm) {
     const uint64_t parts = bv ? bv->nparts : (part_end(L) > L.part_lo ? part_end(L) - L.part_lo : 0);
     if (parts == 0) return cudaSuccess;
     // several partitions per warp; a batch's structures may differ in r (up to 8 bits per value byte)
     const uint32_t R = bv ? 8u * vbytes : L.r;
     const uint32_t G = std::min<uint32_t>(32u / R, (uint32_t)kBsGroups);
-    const uint64_t warps = (parts + G - 1) / G;
-    const unsigned grid = (unsigned)((warps + kBsWarps - 1) / kBsWarps);
-    const BatchView v = bv ? *bv : BatchView();
-    cudaError_t e = vbytes == 1   ? prefer_shared(k_backsub_multi<uint8_t>)
-                    : vbytes == 2 ? prefer_shared(k_backsub_multi<uint16_t>)
-                                  : prefer_shared(k_backsub_multi<uint32_t>);
-    if (e != cudaSuccess) return e;
-    switch (vbytes) {
-    case 1: k_backsub_multi<uint8_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint8_t *)Yg, Z, v, R, G); break;
-    case 2: k_backsub_multi<uint16_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint16_t *)Yg, Z, v, R, G); break;
-    default: k_backsub_multi<uint32_t><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, (const uint32_t *)Yg, Z, v, R, G); break;
+    const uint64_t njobs = (parts + G - 1) / G;
+    uint64_t grid = (njobs + kBsWarps - 1) / kBsWarps;
+    if (max_ctas_per_sm) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = std::min<uint64_t>(grid, (uint64_t)sms * max_ctas_per_sm);
     }
-    return cudaGetLastError();
+    const BatchView v = bv ? *bv : BatchView();
+    switch (vbytes) {
+    case 1: return backsub_impl<uint8_t>(L, Cg, (const uint8_t *)Yg, Z, st, v, R, G, njobs, (unsigned)grid);
+    case 2: return backsub_impl<uint16_t>(L, Cg, (const uint16_t *)Yg, Z, st, v, R, G, njobs, (unsigned)grid);
+    default: return backsub_impl<uint32_t>(L, Cg, (const uint32_t *)Yg, Z, st, v, R, G, njobs, (unsigned)grid);
+    }
 }
 
 }  // namespace burr

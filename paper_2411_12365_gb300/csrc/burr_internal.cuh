@@ -168,8 +168,12 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
                         uint32_t *err, cudaStream_t st, const BatchView *bv = nullptr);
 
 // Back-substitution of every partition: Z from the band.
+// max_ctas_per_sm > 0 caps the grid at that many CTAs per SM (the warps then
+// walk the partitions with the grid's stride), which leaves room beside the
+// back-substitution for the kernels of the next layer.
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
-                           uint64_t *Z, cudaStream_t st, const BatchView *bv = nullptr);
+                           uint64_t *Z, cudaStream_t st, const BatchView *bv = nullptr,
+                           uint32_t max_ctas_per_sm = 0);
 
 // Batched sort: every structure's keys of the layer grouped by global bucket
 // (as records h of each structure's layer).
