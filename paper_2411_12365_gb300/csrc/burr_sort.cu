@@ -256,11 +256,6 @@ __device__ void block_scan(const uint32_t *cnt, uint32_t *out, uint32_t len, uin
     __syncthreads();
 }
 
-// One scatter pass.  Tiles of kTile keys are ordered by digit in shared
-// memory and written as contiguous runs.  Unsegmented (pass 1): digit =
-// group >> dshift over all n keys, cursor[digit].  Segmented (pass 2): tiles
-// stay inside pass-1 bin seg = blockIdx / nseg_ctas, digit = group & (D - 1),
-// cursor[seg * D + digit] (= cursor[group]).
 // Asynchronous global -> shared copies (the tile loads of k_scatter).
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -699,7 +694,7 @@ k_group_sort_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals
     const uint64_t lg = g - D.group_base;
     const uint64_t b_lo = lg << kGroupShift;            // first local bucket of the group
     const uint32_t nbk = (uint32_t)min((uint64_t)kGroupBuckets, D.L.nb - b_lo);
-    const uint64_t sigma = D.L.sigma, range = D.L.range;
+    const uint64_t range = D.L.range;
     const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
     if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
