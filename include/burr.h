@@ -92,7 +92,7 @@ extern "C" {
 #define BURR_FLAG_TEST_WINDOW 2u  /* testing only: the band treats a pivot 136 or more slots past
                                      its bucket's first slot as leaving the on-chip window (the
                                      BURR_ERR_INTERNAL path of a real window overflow, which needs
-                                     a pivot 385 or more slots past its row's start) */
+                                     a pivot 383 or more slots past its row's start) */
 
 typedef struct burr_handle burr_handle;
 

@@ -108,7 +108,7 @@ __device__ __forceinline__ unsigned long long row_tag(uint32_t k) {
 }
 
 struct BandWarpSmem {
-    RingSlot ring[kRing + kLookMax];   // live band window (+ read-ahead pad, never written)
+    RingSlot ring[kRing + kLookMax];   // live band window (+ read-ahead pad: zero, never written)
     uint16_t clist[kRing];         // ring indices stored by the current set (rollback)
     StagedRow rows[kStage];        // staged equations, ascending offset
     uint32_t first[132];           // first staged index of each offset (+ [128] = count)
@@ -147,10 +147,13 @@ struct Ctx {
 
 enum { kOk = 0, kDependent = 1, kOverflow = 2 };
 
-// Pivots at or past bucket start + this many slots leave the live window (the
-// ring, unless a test asked for a smaller window).
+// Pivots at or past bucket start + this many slots leave the live window: the
+// ring less the read-ahead, so that the slots a step reads ahead of its pivot
+// are still inside the window and never alias the window's first slots (a
+// smaller window when a test asks for one).
+constexpr uint32_t kWindow = (uint32_t)(kRing - kLookMax);
 __device__ __forceinline__ uint32_t window_of(const LayerDesc &L) {
-    return L.window ? min(L.window, (uint32_t)kRing) : (uint32_t)kRing;
+    return L.window ? min(L.window, kWindow) : kWindow;
 }
 
 __device__ __forceinline__ void rollback(BandWarpSmem &S, uint32_t ncommit, int lane) {
@@ -274,7 +277,9 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
     if (hi <= lo) return kOk;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&S.ring[0]);
-    uint32_t next = lo + 32u, nc = S.ncommit;
+    uint32_t nc = S.ncommit;
+    // tagged: index of the next row to hand out; untagged: that index less the rows stored
+    uint32_t next = kTag ? lo + 32u : lo + 32u - nc;
     bool has = lo + (uint32_t)lane < hi;
     // a lane without a row swaps (0, 0) in, which leaves every slot as it was
     unsigned long long cur = 0, y = 0;
@@ -292,9 +297,9 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
     for (;;) {
         const uint32_t ri = pos & kRingMask;
         const unsigned addr = ring0 + ri * (unsigned)sizeof(RingSlot);
-        // A read-ahead slot past the live window would alias an older slot, and one past the
-        // ring's end is the pad: near either, no read-ahead slot is used.
-        const bool win = pos - bB + (uint32_t)kLook < (uint32_t)kRing && ri + (uint32_t)kLook < (uint32_t)kRing;
+        // Read-ahead: the pivot lies below bB + wlim <= bB + kRing - kLook, so the slots read
+        // ahead are inside the window; past the ring's end they are the zero pad, which reads
+        // as empty (the step then ends there, and the next swap goes to the true slot).
         unsigned long long oc, oy;
         unsigned long long lc[kLook > 0 ? kLook : 1], ly[kLook > 0 ? kLook : 1];
 #pragma unroll
@@ -305,16 +310,18 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 
         // Hand-out first: the next row's shared read is in flight during the elimination.
         const bool take = stored || (kTag && pend);
+        // untagged, every stored row frees its lane for the next row: the next row handed out
+        // is row lo + 32 + (rows stored so far), and a lane's commit-list entry gives its index
         const unsigned sm = __ballot_sync(kFull, stored);
         const unsigned tm = kTag ? __ballot_sync(kFull, take) : sm;
-        const uint32_t rank = (uint32_t)__popc(sm & lt);
-        const uint32_t nidx = next + (kTag ? (uint32_t)__popc(tm & lt) : rank);
+        const uint32_t ci = nc + (uint32_t)__popc(sm & lt);
+        const uint32_t nidx = kTag ? next + (uint32_t)__popc(tm & lt) : ci + next;
         const bool nhas = take && nidx < hi;
         StagedRow nr = StagedRow{0ull, 0u, 0u};
         if (nhas) nr = S.rows[nidx];
-        if (stored) S.clist[nc + rank] = (uint16_t)ri;
+        if (stored) S.clist[ci] = (uint16_t)ri;
         nc += (uint32_t)__popc(sm);
-        next += (uint32_t)__popc(tm);
+        if (kTag) next += (uint32_t)__popc(tm);
 
         // Elimination for lanes whose swap returned a stored row: against that row, then through
         // the read-ahead slots.  The row is (over : hi32 : lo32), bit j = slot pos + j; bit 0 is
@@ -326,7 +333,7 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         uint32_t over = 0;
         uint32_t y2 = (uint32_t)y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits
         uint32_t yh = kTag ? (uint32_t)(y >> 32) ^ (uint32_t)(oy >> 32) : 0u;   // tags (bits 1..)
-        bool go = win;
+        bool go = true;
         bool use[kLook > 0 ? kLook : 1];
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
     const uint64_t own_lo = part_own_lo(L, part);
     const uint64_t own_hi = part_own_hi(L, part);
 
-    for (int i = lane; i < kRing; i += 32) {
+    for (int i = lane; i < kRing + kLookMax; i += 32) {   // the ring and its pad
         S.ring[i].c = 0;
         S.ring[i].y = 0;
     }
