@@ -93,6 +93,10 @@ extern "C" {
                                      its bucket's first slot as leaving the on-chip window (the
                                      BURR_ERR_INTERNAL path of a real window overflow, which needs
                                      a pivot 383 or more slots past its row's start) */
+#define BURR_FLAG_TEST_SLACK 4u   /* testing only: a layer sorted in two scatter passes (more than
+                                     2^16 buckets) sorts into bins of half their expected size, so
+                                     that they overflow and the layer is sorted again exactly (the
+                                     structure is the same either way) */
 
 typedef struct burr_handle burr_handle;
 

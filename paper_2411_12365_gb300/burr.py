@@ -20,6 +20,7 @@ ERR_INVALID, ERR_OOM, ERR_UNSOLVABLE, ERR_TIMEOUT, ERR_CUDA, ERR_INTERNAL = -1, 
 MAX_LAYERS = 8
 FLAG_TIMING = 1
 FLAG_TEST_WINDOW = 2
+FLAG_TEST_SLACK = 4
 THRESH_2BIT, THRESH_1PLUS = 0, 1
 CUT_NONE, CUT_MINBUMP, CUT_MAXPREV, CUT_DIFF = 0, 1, 2, 3
 

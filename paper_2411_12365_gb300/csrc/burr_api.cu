@@ -312,6 +312,7 @@ LayerDesc make_desc(const burr_params &p, uint32_t r, uint64_t n, uint64_t m, ui
     L.vmask = r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
     L.mode = p.threshold_mode;
     L.window = (p.flags & BURR_FLAG_TEST_WINDOW) ? kTestWindow : 0u;
+    L.test_slack = (p.flags & BURR_FLAG_TEST_SLACK) ? 1u : 0u;
     return L;
 }
 
@@ -367,6 +368,13 @@ constexpr uint32_t kBacksubCtasPerSm = BURR_BACKSUB_CTAS_PER_SM;
 #define BURR_BAND_SPLIT 90
 #endif
 constexpr uint32_t kBandSplitPct = BURR_BAND_SPLIT;
+// Layers sorted in two scatter passes use fixed-capacity bins instead of
+// counting passes (launch_sort_slack_*), with an exact sort again if a bin
+// overflowed; 0 turns this off.
+#ifndef BURR_SORT_SLACK
+#define BURR_SORT_SLACK 1
+#endif
+constexpr bool kSortSlack = BURR_SORT_SLACK != 0;
 constexpr int kOrderSlot = kBandSets;      // event slots after the per-set ones
 constexpr int kJoinSlot = kBandSets + 1;
 constexpr int kFinalSlot = kBandSets + 2;
@@ -445,7 +453,14 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     CK(ar.alloc(&sk, n * 8), "alloc sorted keys");
     CK(ar.alloc(&sv, n * vb), "alloc sorted values");
     CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
-    CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
+    // the exact sort's scratch, or the fixed-capacity sort's for layer 0 if larger
+    size_t ss_bytes = sort_scratch_bytes(n, cap_m, vb);
+    if (kSortSlack && n > 0 && m0 < (1ull << 32)) {
+        const uint64_t K0 = num_partitions(m0, layer_partition_slots(p, 0), p.min_partition_slots);
+        const LayerDesc L0 = make_desc(p, r, n, m0, layer_seed(p.seed, 0), K0, false, layer_partition_slots(p, 0));
+        ss_bytes = std::max(ss_bytes, sort_slack_scratch_bytes(L0, vb));
+    }
+    CK(ar.alloc(&ss, ss_bytes), "alloc sort scratch");
     void *cgs[kBandSets] = {}, *ygs[kBandSets] = {};
     uint64_t cgcap[kBandSets] = {};
     CK(ar.alloc(&cg, cap_m * 8), "alloc band");
@@ -545,51 +560,71 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         }
         // the band of layer l overwrites the set that layer l-3 solved: wait for it
         CK(side.reuse(set), "order");
-        tev[l][0] = tm.mark();
-        CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
-        CK(start_backsub(), "backsub");   // the previous layer's, now that this layer's sort is queued
-        if (search) {
-            CK(launch_cut_search(L, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search, p.cut_search_range,
-                                 const_cast<uint32_t *>(L.cuts), st),
-               "cut search");
-            h->launches += 1;
-        }
-        tev[l][1] = tm.mark();
-        LayerDesc Lpend = L;
-        const uint64_t K1 = kBandSplitPct && side.band2 && !search ? S.K * kBandSplitPct / 100 : 0;
-        if (K1 > 0 && K1 < S.K && S.K >= 4096) {
-            // first launch on the build stream, second on its own stream (started together, so
-            // the second one's partitions fill the SMs the first one's last partitions leave);
-            // the first launch's back-substitution follows it on the side stream
-            LayerDesc La = L, Lb = L;
-            La.part_hi = (uint32_t)K1;
-            Lb.part_lo = (uint32_t)K1;
-            CK(side.order(st, side.band2, kSplitSlot), "order");
-            CK(launch_band(La, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
-                           S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
-            CK(launch_band(Lb, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
-                           S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, side.band2), "band");
-            CK(side.order(st, side.side, kOrderSlot), "order");
-            tev[l][5] = tm.mark_on(side.side);
-            CK(launch_backsub(La, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side, nullptr, kBacksubCtasPerSm),
-               "backsub");
-            tev[l][6] = tm.mark_on(side.side);
-            CK(side.order(side.band2, st, kSplitEndSlot), "order");
-            Lpend = Lb;
-            h->launches += 2;
-        } else {
-            CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
-                           S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
-        }
-        tev[l][2] = tm.mark();
-        if (onep) CK(launch_thresh_flags(tex, dseg, blkseg, (uint32_t)nd, S.flags, tcounts, S.dir, st), "flags");
-        pending = PendingBacksub{true, l, set, Lpend, S.z};
-        h->launches += sort_kernel_count(L) + 2 + (onep ? 2 : 0);
+        // sorted with fixed-capacity bins where they fit the scratch; if a bin overflowed
+        // (kErrSortSlack at the end of the layer), the layer is sorted and banded again exactly
+        const size_t slack_bytes = kSortSlack ? sort_slack_scratch_bytes(L, vb) : 0;
+        bool slack = slack_bytes != 0 && slack_bytes <= ss_bytes;
         unsigned long long hc[2] = {0, 0};
         uint32_t nflag = 0;
-        CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
-        if (onep) CK(cudaMemcpyAsync(&nflag, S.dir + nd, 4, cudaMemcpyDeviceToHost, st), "read threshold count");
-        CK(cudaStreamSynchronize(st), "layer");
+        for (;;) {
+            tev[l][0] = tm.mark();
+            if (slack) {
+                CK(launch_sort_slack_begin(L, vb, ss, st), "sort");
+                CK(launch_sort_slack_pass1(L, vb, cur_k, cur_v, 0, cur_n, ss, err, st), "sort");
+                CK(launch_sort_slack_end(L, vb, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+            } else {
+                CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
+            }
+            CK(start_backsub(), "backsub");   // the previous layer's, now that this layer's sort is queued
+            if (search) {
+                CK(launch_cut_search(L, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search, p.cut_search_range,
+                                     const_cast<uint32_t *>(L.cuts), st),
+                   "cut search");
+                h->launches += 1;
+            }
+            tev[l][1] = tm.mark();
+            LayerDesc Lpend = L;
+            const uint64_t K1 = kBandSplitPct && side.band2 && !search ? S.K * kBandSplitPct / 100 : 0;
+            if (K1 > 0 && K1 < S.K && S.K >= 4096) {
+                // first launch on the build stream, second on its own stream (started together, so
+                // the second one's partitions fill the SMs the first one's last partitions leave);
+                // the first launch's back-substitution follows it on the side stream
+                LayerDesc La = L, Lb = L;
+                La.part_hi = (uint32_t)K1;
+                Lb.part_lo = (uint32_t)K1;
+                CK(side.order(st, side.band2, kSplitSlot), "order");
+                CK(launch_band(La, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
+                               S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
+                CK(launch_band(Lb, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
+                               S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, side.band2), "band");
+                CK(side.order(st, side.side, kOrderSlot), "order");
+                tev[l][5] = tm.mark_on(side.side);
+                CK(launch_backsub(La, vb, (const uint64_t *)cgs[set], ygs[set], S.z, side.side, nullptr,
+                                  kBacksubCtasPerSm),
+                   "backsub");
+                tev[l][6] = tm.mark_on(side.side);
+                CK(side.order(side.band2, st, kSplitEndSlot), "order");
+                Lpend = Lb;
+                h->launches += 2;
+            } else {
+                CK(launch_band(L, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cgs[set], ygs[set],
+                               S.thresh, tex, (uint64_t *)bk[which], bv[which], bcount, err, st), "band");
+            }
+            tev[l][2] = tm.mark();
+            if (onep) CK(launch_thresh_flags(tex, dseg, blkseg, (uint32_t)nd, S.flags, tcounts, S.dir, st), "flags");
+            pending = PendingBacksub{true, l, set, Lpend, S.z};
+            h->launches += (slack ? 6 : sort_kernel_count(L)) + 2 + (onep ? 2 : 0);
+            CK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, st), "read counters");
+            if (onep) CK(cudaMemcpyAsync(&nflag, S.dir + nd, 4, cudaMemcpyDeviceToHost, st), "read threshold count");
+            CK(cudaStreamSynchronize(st), "layer");
+            if (!(hc[1] & kErrSortSlack)) break;
+            // a bin overflowed: this layer's outputs are partial; sort and band it again exactly
+            slack = false;
+            pending.on = false;
+            CK(cudaStreamSynchronize(side.side), "layer");   // a split band's first back-substitution
+            if (!onep) CK(cudaMemsetAsync(S.thresh, 0, tw * 8, st), "clear thresholds");
+            CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
+        }
         const uint32_t e = (uint32_t)(hc[1] & 0xffffffffu);
         if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band window (510 slots)", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
@@ -639,7 +674,8 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
                 cap_m = F.m;
                 cap_nb = num_buckets(cap_m, p.bucket_slots);
                 CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
-                CK(ar.alloc(&ss, sort_scratch_bytes(n, cap_m, vb)), "alloc sort scratch");
+                ss_bytes = sort_scratch_bytes(n, cap_m, vb);
+                CK(ar.alloc(&ss, ss_bytes), "alloc sort scratch");
             }
             CK(side.reuse(set), "order");
             CK(dev_alloc((void **)&F.z, (F.m / 64) * r * 8, st), "alloc table");

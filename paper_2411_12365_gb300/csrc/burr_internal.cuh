@@ -17,7 +17,7 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 // error bits written by kernels into the build's device error word
 constexpr uint32_t kErrRingOverflow = 1u;         // a pivot left the on-chip window
 constexpr uint32_t kErrUnsolvable = 2u;           // base case: an equation was dependent
-constexpr uint32_t kErrBucketSort = 4u;           // a level-2 sort bin exceeded its capacity
+constexpr uint32_t kErrSortSlack = 4u;            // a sort bin of fixed capacity overflowed (sort again exactly)
 
 // SplitMix64 output function (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -97,6 +97,7 @@ struct LayerDesc {
     uint32_t vmask;      // (1 << r) - 1
     uint32_t mode;       // BURR_THRESH_2BIT or BURR_THRESH_1PLUS
     uint32_t window;     // pivots at or past bucket start + window leave the band's window (0 = the whole ring)
+    uint32_t test_slack; // 1: the fixed-capacity sort bins get half their expected size (testing the exact redo)
     uint32_t part_lo;    // band and back-substitution launches cover partitions [part_lo, part_hi)
     uint32_t part_hi;    // (0: up to K); a shard of a sharded build owns such a range
     const uint32_t *cuts;  // device: first bucket of each partition, [K] = nb; nullptr: partition j at j*P
@@ -158,6 +159,20 @@ uint32_t sort_kernel_count(const LayerDesc &L);
 cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
                         uint64_t *keys_out, void *vals_out, uint32_t *bucket_start, void *scratch,
                         uint32_t *err, cudaStream_t st, bool out_keys = false);
+
+// The same sort without its counting passes, for layers sorted in two
+// scatter passes (sort_slack_scratch_bytes is 0 for the others): bins of fixed
+// capacity, sized from the binomial spread of the keys' uniform start slots.
+// begin, then pass 1 over input ranges [lo, hi) that together cover [0, n)
+// (in any order, each once), then end.  If a bin overflowed, *err gets
+// kErrSortSlack and the output holds only part of the keys (each in its right
+// place): the caller sorts again with launch_sort.
+size_t sort_slack_scratch_bytes(const LayerDesc &L, uint32_t vbytes);
+cudaError_t launch_sort_slack_begin(const LayerDesc &L, uint32_t vbytes, void *scratch, cudaStream_t st);
+cudaError_t launch_sort_slack_pass1(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                                    uint64_t lo, uint64_t hi, void *scratch, uint32_t *err, cudaStream_t st);
+cudaError_t launch_sort_slack_end(const LayerDesc &L, uint32_t vbytes, uint64_t *keys_out, void *vals_out,
+                                  uint32_t *bucket_start, void *scratch, uint32_t *err, cudaStream_t st);
 
 // Band + bump (or base case), writing the band of every partition to Cg/Yg.
 // With a batch view (bv != nullptr) L is ignored: every partition of every

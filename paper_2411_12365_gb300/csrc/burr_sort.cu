@@ -21,6 +21,7 @@
 // slot with one multiply-high and the coefficients with one more round,
 // instead of hashing the key again in every pass; the band recovers the key
 // only for the rows it bumps.  The stage entry points ask for keys instead.
+#include <cmath>
 #include <cstdio>
 
 #include "burr_internal.cuh"
@@ -290,12 +291,20 @@ constexpr size_t scatter_smem_bytes() {
 //
 // RAW: the input holds keys, and the pass writes records h = mix64(key ^
 // sigma); otherwise the input already holds records.
-template <typename V, bool SEG, bool RAW>
+//
+// SLACK: output bin c (digit, or group for pass 2) is the fixed range
+// [c * cap_out, (c + 1) * cap_out), its cursor starting at c * cap_out; a key
+// that would land past its bin's end is dropped and kErrSortSlack is raised.
+// Pass 2 then reads pass-1 bin seg from [seg * cap_in, min(off1[seg],
+// (seg + 1) * cap_in)) (off1 = the pass-1 cursors).  n is the input array's
+// length; pass 1 reads [in_lo, n).
+template <typename V, bool SEG, bool RAW, bool SLACK = false>
 __global__ void __launch_bounds__(kTileThreads, kTileCtas)
 k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_t n,
           const uint32_t *__restrict__ off1, uint32_t nseg_ctas, uint64_t sigma, uint64_t range, uint32_t gshift,
           uint32_t dshift, uint32_t D, uint32_t *__restrict__ cursor, uint64_t *__restrict__ keys_out,
-          V *__restrict__ vals_out) {
+          V *__restrict__ vals_out, uint64_t cap_in = 0, uint64_t cap_out = 0, uint32_t *__restrict__ err = nullptr,
+          uint64_t in_lo = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
     V *sval = reinterpret_cast<V *>(skey + kTile);
@@ -303,14 +312,19 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
     unsigned char *ival = reinterpret_cast<unsigned char *>(ikey + kTile);
     __shared__ uint32_t hist[kMaxDigits], excl[kMaxDigits], gbase[kMaxDigits], warp_sums[32];
 
-    uint64_t lo = 0, hi = n;
+    uint64_t lo = in_lo, hi = n;
     uint32_t seg = 0, part = blockIdx.x, nparts = gridDim.x;
     if (SEG) {
         seg = blockIdx.x / nseg_ctas;
         part = blockIdx.x % nseg_ctas;
         nparts = nseg_ctas;
-        lo = off1[seg];
-        hi = off1[seg + 1];
+        if (SLACK) {
+            lo = (uint64_t)seg * cap_in;
+            hi = min((uint64_t)off1[seg], lo + cap_in);
+        } else {
+            lo = off1[seg];
+            hi = off1[seg + 1];
+        }
     }
     const bool vals_aligned = ((uintptr_t)vals & 3u) == 0;
     // start the copy of tile t into the input buffer; returns whether its values are copied too
@@ -393,6 +407,10 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
             const uint32_t g = group_of_h(h, range, gshift);
             const uint32_t d = SEG ? (g & (D - 1)) : (g >> dshift);
             const uint32_t dst = gbase[d] + (i - excl[d]);
+            if (SLACK && dst >= ((uint64_t)seg * (SEG ? D : 0) + d + 1) * cap_out) {
+                atomicOr(err, kErrSortSlack);
+                continue;
+            }
             keys_out[dst] = h;
             vals_out[dst] = sval[i];
         }
@@ -420,11 +438,13 @@ __device__ __forceinline__ uint64_t group_out(uint64_t x, uint64_t sigma) {
     if (RAW) return OUT_KEYS ? x : mix64(x ^ sigma);
     return OUT_KEYS ? key_of_h(x, sigma) : x;
 }
-template <typename V, bool RAW, bool OUT_KEYS>
+// SLACK: the input of group g starts at g * cap (the bins of a SLACK pass 2),
+// and goff holds the packed offsets of the groups' counts.
+template <typename V, bool RAW, bool OUT_KEYS, bool SLACK = false>
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, const uint32_t *__restrict__ goff,
              uint64_t sigma, uint64_t range, uint32_t log2B, uint64_t nb, uint64_t *__restrict__ keys_out,
-             V *__restrict__ vals_out, uint32_t *__restrict__ bucket_start) {
+             V *__restrict__ vals_out, uint32_t *__restrict__ bucket_start, uint64_t cap = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(smem_raw);
     V *sval = reinterpret_cast<V *>(skey + kGroupCap);
@@ -433,6 +453,10 @@ k_group_sort(const uint64_t *__restrict__ keys, const V *__restrict__ vals, cons
     const uint64_t b_lo = g << kGroupShift;
     const uint32_t nbk = (uint32_t)min((uint64_t)kGroupBuckets, nb - b_lo);
     const uint32_t lo = goff[g], hi = goff[g + 1], n = hi - lo;
+    if (SLACK) {   // index i in [lo, hi) reads input g * cap + (i - lo)
+        keys += g * cap - lo;
+        vals += g * cap - lo;
+    }
     if (threadIdx.x < kGroupBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
     {
@@ -516,18 +540,46 @@ Scratch carve(void *scratch, uint64_t n, uint64_t ngroups, uint32_t vbytes) {
 }
 
 // The group pass of sort_impl: RAW when it reads the caller's keys (a layer
-// of one group), OUT_KEYS when it writes keys instead of records.
-template <typename V, bool RAW, bool OUT_KEYS>
+// of one group), OUT_KEYS when it writes keys instead of records; SLACK (with
+// the bins' capacity cap) as k_group_sort.
+template <typename V, bool RAW, bool OUT_KEYS, bool SLACK = false>
 cudaError_t launch_group_sort(const Plan &P, const LayerDesc &L, const uint64_t *gk, const V *gv, const uint32_t *goff,
-                              uint64_t *keys_out, V *vals_out, uint32_t *bucket_start, cudaStream_t st) {
+                              uint64_t *keys_out, V *vals_out, uint32_t *bucket_start, cudaStream_t st,
+                              uint64_t cap = 0) {
     const size_t group_smem = (size_t)kGroupCap * (8 + sizeof(V));
-    cudaError_t e = func_attr(k_group_sort<V, RAW, OUT_KEYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = func_attr(k_group_sort<V, RAW, OUT_KEYS, SLACK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)group_smem);
     if (e != cudaSuccess) return e;
-    if ((e = prefer_shared(k_group_sort<V, RAW, OUT_KEYS>)) != cudaSuccess) return e;
-    k_group_sort<V, RAW, OUT_KEYS><<<(unsigned)P.ngroups, kGroupThreads, group_smem, st>>>(
-        gk, gv, goff, L.sigma, L.range, P.log2B, L.nb, keys_out, vals_out, bucket_start);
+    if ((e = prefer_shared(k_group_sort<V, RAW, OUT_KEYS, SLACK>)) != cudaSuccess) return e;
+    k_group_sort<V, RAW, OUT_KEYS, SLACK><<<(unsigned)P.ngroups, kGroupThreads, group_smem, st>>>(
+        gk, gv, goff, L.sigma, L.range, P.log2B, L.nb, keys_out, vals_out, bucket_start, cap);
     return cudaGetLastError();
+}
+
+// CTAs per pass-1 bin in the second pass: enough for about eight waves of the
+// resident CTAs, so that the last wave leaves few SMs idle (with one CTA per
+// bin and more bins than resident CTAs, the second wave ran half empty).
+uint32_t seg_ctas(const Plan &P) {
+    const unsigned sms = (unsigned)num_sms();
+    uint64_t per64 = (8ull * sms * (uint64_t)kTileCtas + P.D1 - 1) / P.D1;
+    if (per64 > 64) per64 = 64;
+    if (per64 < 1) per64 = 1;
+    return (uint32_t)per64;
+}
+
+template <typename V>
+cudaError_t sort_attrs_slack() {
+    const int tile_smem = (int)scatter_smem_bytes<V>();
+    cudaError_t e;
+    if ((e = func_attr(k_scatter<V, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem)) !=
+            cudaSuccess ||
+        (e = func_attr(k_scatter<V, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem)) !=
+            cudaSuccess ||
+        (e = prefer_shared(k_scatter<V, false, true, true>)) != cudaSuccess ||
+        (e = prefer_shared(k_scatter<V, true, false, true>)) != cudaSuccess ||
+        (e = prefer_shared(k_scan)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
 template <typename V>
@@ -578,13 +630,7 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
         k_scan<<<1, 1024, 0, st>>>(S.c1, P.D1, S.o1, S.u1);
         k_scatter<V, false, true><<<grid_for(n, kTile, sms * kTileCtas), kTileThreads, tile_smem, st>>>(
             keys, vals, n, nullptr, 1, L.sigma, L.range, P.gshift, P.d2, P.D1, S.u1, keys_out, vals_out);
-        // CTAs per pass-1 bin: enough for about eight waves of the resident CTAs,
-        // so that the last wave leaves few SMs idle (with one CTA per bin and
-        // more bins than resident CTAs, the second wave ran half empty)
-        uint64_t per64 = (8ull * sms * (uint64_t)kTileCtas + P.D1 - 1) / P.D1;
-        if (per64 > 64) per64 = 64;
-        if (per64 < 1) per64 = 1;
-        const uint32_t per = (uint32_t)per64;
+        const uint32_t per = seg_ctas(P);
         k_hist_seg<<<P.D1 * per, kHistThreads, 0, st>>>(keys_out, S.o1, per, L.sigma, L.range, P.gshift, P.D2,
                                                          S.c2);
         k_scan<<<1, 1024, 0, st>>>(S.c2, (uint32_t)P.ngroups, S.o2, S.u2);
@@ -598,6 +644,142 @@ cudaError_t sort_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, u
                                                         bucket_start, st)
                     : launch_group_sort<V, false, false>(P, L, S.keys, (const V *)S.vals, goff, keys_out, vals_out,
                                                          bucket_start, st);
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass layers without counting passes.  The start slots of a layer's keys
+// are uniform over [0, range) (one multiply-high of a 64-bit hash), so the
+// number of keys in a pass-1 bin or a sort group is binomial with a known
+// mean mu.  Each bin and group gets a fixed range of mu + 8 sqrt(mu) + a
+// margin slots in scratch, and the scatter passes reserve space in it with
+// the same per-tile atomics as the exact sort: no histogram pass over the
+// keys is needed before either scatter.  A key that would fall past its
+// range's end (never seen with distinct keys: 8 standard deviations) is
+// dropped and kErrSortSlack is raised; everything that is written is in its
+// right bin, so the layer can go on, and the caller sorts it again exactly.
+// The group pass packs the groups back to back (offsets from a scan of their
+// counts), so the output is the exact sort's.
+// ---------------------------------------------------------------------------
+
+struct SlackPlan {
+    Plan P;
+    uint64_t cap1 = 0, cap2 = 0;   // slots of a pass-1 bin and of a group
+    bool ok = false;
+};
+
+SlackPlan make_slack_plan(const LayerDesc &L) {
+    SlackPlan S;
+    S.P = make_plan(L);
+    if (S.P.passes != 2 || L.range == 0 || L.n == 0) return S;
+    const double mu1 = (double)L.n * (double)((uint64_t)S.P.D2 << S.P.gshift) / (double)L.range;
+    const double mu2 = (double)L.n * (double)(1ull << S.P.gshift) / (double)L.range;
+    S.cap1 = L.test_slack ? (uint64_t)(mu1 / 2) + 1 : (uint64_t)(mu1 + 8.0 * sqrt(mu1)) + 256;
+    S.cap2 = L.test_slack ? (uint64_t)(mu2 / 2) + 1 : (uint64_t)(mu2 + 8.0 * sqrt(mu2)) + 64;
+    // groups must fit the group pass's shared memory, positions 32 bits
+    S.ok = S.cap2 <= kGroupCap && (double)S.P.D1 * (double)S.cap1 < 4.0e9 &&
+           (double)S.P.ngroups * (double)S.cap2 < 4.0e9;
+    return S;
+}
+
+struct SlackScratch {
+    uint64_t *keys1, *keys2;
+    void *vals1, *vals2;
+    uint32_t *cur1, *cur2, *cnt, *off, *tmp;
+};
+
+size_t slack_bytes(const SlackPlan &S, uint32_t vbytes, SlackScratch *out) {
+    const uint64_t n1 = (uint64_t)S.P.D1 * S.cap1, n2 = S.P.ngroups * S.cap2, G = S.P.ngroups;
+    size_t o = 0;
+    SlackScratch x;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    const size_t k1 = take(n1 * 8), v1 = take(n1 * vbytes), k2 = take(n2 * 8), v2 = take(n2 * vbytes),
+                 c1 = take((size_t)S.P.D1 * 4), c2 = take(G * 4), cn = take((G + 1) * 4), of = take((G + 1) * 4),
+                 tp = take((G + 1) * 4);
+    if (out) {
+        char *b = (char *)out->keys1;   // the scratch base, passed in keys1
+        x.keys1 = (uint64_t *)(b + k1);
+        x.vals1 = b + v1;
+        x.keys2 = (uint64_t *)(b + k2);
+        x.vals2 = b + v2;
+        x.cur1 = (uint32_t *)(b + c1);
+        x.cur2 = (uint32_t *)(b + c2);
+        x.cnt = (uint32_t *)(b + cn);
+        x.off = (uint32_t *)(b + of);
+        x.tmp = (uint32_t *)(b + tp);
+        *out = x;
+    }
+    return o;
+}
+
+SlackScratch slack_carve(const SlackPlan &S, uint32_t vbytes, void *scratch) {
+    SlackScratch x;
+    x.keys1 = (uint64_t *)scratch;
+    slack_bytes(S, vbytes, &x);
+    return x;
+}
+
+// cursor of pass-1 bin d = d * cap1, of group g = g * cap2
+__global__ void k_slack_init(uint32_t *__restrict__ cur1, uint32_t D1, uint64_t cap1, uint32_t *__restrict__ cur2,
+                             uint64_t G, uint64_t cap2) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D1 + G; i += stride) {
+        if (i < D1) cur1[i] = (uint32_t)(i * cap1);
+        else cur2[i - D1] = (uint32_t)((i - D1) * cap2);
+    }
+}
+
+// keys each group holds (its cursor's advance, at most its capacity)
+__global__ void k_slack_counts(const uint32_t *__restrict__ cur2, uint64_t G, uint64_t cap2, uint32_t *__restrict__ cnt,
+                               uint32_t *__restrict__ err) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride) {
+        uint64_t c = cur2[g] - g * cap2;
+        if (c > cap2) {
+            c = cap2;
+            atomicOr(err, kErrSortSlack);
+        }
+        cnt[g] = (uint32_t)c;
+    }
+}
+
+template <typename V>
+cudaError_t slack_begin_impl(const SlackPlan &S, const SlackScratch &X, cudaStream_t st) {
+    cudaError_t e = sort_attrs_slack<V>();
+    if (e != cudaSuccess) return e;
+    k_slack_init<<<grid_for(S.P.D1 + S.P.ngroups, 256, 1024), 256, 0, st>>>(X.cur1, S.P.D1, S.cap1, X.cur2,
+                                                                             S.P.ngroups, S.cap2);
+    return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t slack_pass1_impl(const LayerDesc &L, const SlackPlan &S, const SlackScratch &X, const uint64_t *keys,
+                             const V *vals, uint64_t lo, uint64_t hi, uint32_t *err, cudaStream_t st) {
+    if (hi <= lo) return cudaSuccess;
+    const unsigned sms = (unsigned)num_sms();
+    k_scatter<V, false, true, true><<<grid_for(hi - lo, kTile, sms * kTileCtas), kTileThreads, scatter_smem_bytes<V>(),
+                                      st>>>(keys, vals, hi, nullptr, 1, L.sigma, L.range, S.P.gshift, S.P.d2, S.P.D1,
+                                            X.cur1, X.keys1, (V *)X.vals1, 0, S.cap1, err, lo);
+    return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t slack_end_impl(const LayerDesc &L, const SlackPlan &S, const SlackScratch &X, uint64_t *keys_out,
+                           V *vals_out, uint32_t *bucket_start, uint32_t *err, cudaStream_t st) {
+    const Plan &P = S.P;
+    const uint32_t per = seg_ctas(P);
+    k_scatter<V, true, false, true><<<P.D1 * per, kTileThreads, scatter_smem_bytes<V>(), st>>>(
+        X.keys1, (const V *)X.vals1, (uint64_t)P.D1 * S.cap1, X.cur1, per, L.sigma, L.range, P.gshift, 0, P.D2, X.cur2,
+        X.keys2, (V *)X.vals2, S.cap1, S.cap2, err);
+    k_slack_counts<<<grid_for(P.ngroups, 256, 1024), 256, 0, st>>>(X.cur2, P.ngroups, S.cap2, X.cnt, err);
+    k_scan<<<1, 1024, 0, st>>>(X.cnt, (uint32_t)P.ngroups, X.off, X.tmp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_group_sort<V, false, false, true>(P, L, X.keys2, (const V *)X.vals2, X.off, keys_out, vals_out,
+                                                    bucket_start, st, S.cap2);
 }
 
 // ---------------------------------------------------------------------------
@@ -818,6 +1000,46 @@ cudaError_t launch_sort_batch(const BatchView &bv, uint32_t vbytes, const uint64
 uint32_t sort_kernel_count(const LayerDesc &L) {
     const Plan P = make_plan(L);
     return P.passes == 0 ? 1u : (P.passes == 1 ? 4u : 7u);
+}
+
+size_t sort_slack_scratch_bytes(const LayerDesc &L, uint32_t vbytes) {
+    const SlackPlan S = make_slack_plan(L);
+    return S.ok ? slack_bytes(S, vbytes, nullptr) : 0;
+}
+
+cudaError_t launch_sort_slack_begin(const LayerDesc &L, uint32_t vbytes, void *scratch, cudaStream_t st) {
+    const SlackPlan S = make_slack_plan(L);
+    if (!S.ok) return cudaErrorInvalidValue;
+    const SlackScratch X = slack_carve(S, vbytes, scratch);
+    switch (vbytes) {
+    case 1: return slack_begin_impl<uint8_t>(S, X, st);
+    case 2: return slack_begin_impl<uint16_t>(S, X, st);
+    default: return slack_begin_impl<uint32_t>(S, X, st);
+    }
+}
+
+cudaError_t launch_sort_slack_pass1(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,
+                                    uint64_t lo, uint64_t hi, void *scratch, uint32_t *err, cudaStream_t st) {
+    const SlackPlan S = make_slack_plan(L);
+    if (!S.ok || hi > L.n) return cudaErrorInvalidValue;
+    const SlackScratch X = slack_carve(S, vbytes, scratch);
+    switch (vbytes) {
+    case 1: return slack_pass1_impl<uint8_t>(L, S, X, keys, (const uint8_t *)vals, lo, hi, err, st);
+    case 2: return slack_pass1_impl<uint16_t>(L, S, X, keys, (const uint16_t *)vals, lo, hi, err, st);
+    default: return slack_pass1_impl<uint32_t>(L, S, X, keys, (const uint32_t *)vals, lo, hi, err, st);
+    }
+}
+
+cudaError_t launch_sort_slack_end(const LayerDesc &L, uint32_t vbytes, uint64_t *keys_out, void *vals_out,
+                                  uint32_t *bucket_start, void *scratch, uint32_t *err, cudaStream_t st) {
+    const SlackPlan S = make_slack_plan(L);
+    if (!S.ok) return cudaErrorInvalidValue;
+    const SlackScratch X = slack_carve(S, vbytes, scratch);
+    switch (vbytes) {
+    case 1: return slack_end_impl<uint8_t>(L, S, X, keys_out, (uint8_t *)vals_out, bucket_start, err, st);
+    case 2: return slack_end_impl<uint16_t>(L, S, X, keys_out, (uint16_t *)vals_out, bucket_start, err, st);
+    default: return slack_end_impl<uint32_t>(L, S, X, keys_out, (uint32_t *)vals_out, bucket_start, err, st);
+    }
 }
 
 cudaError_t launch_sort(const LayerDesc &L, uint32_t vbytes, const uint64_t *keys, const void *vals,

@@ -65,9 +65,9 @@ def test_stage_sort_groups_by_bucket(n, r):
     assert np.array_equal(ok[a], sk[b]) and np.array_equal(ov[a], sv[b])
 
 
-def _check_build(n, r, seed=I.KEY_SEED, **params):
+def _check_build(n, r, seed=I.KEY_SEED, flags=0, **params):
     keys, vals = _kv(n, r, seed=seed)
-    h = burr.build(keys, vals, r, **params)
+    h = burr.build(keys, vals, r, flags=flags, **params)
     got = h.export()
     names = {"load_factor": "alpha", "fallback_max_retries": "fb_max_retries", "fallback_slack": "fb_slack",
              "bucket_slots": "B"}
@@ -206,6 +206,27 @@ def test_1plus_10m_whole_structure_and_space():
     assert np.array_equal(_vals_np(h1.query(neg)), ref.query(_u64(neg)))
     h2 = burr.build(keys, vals, r)
     assert h1.size_bytes() < h2.size_bytes()               # the point of 1+-bit thresholds
+
+
+# Layers sorted in two scatter passes (more than 2^16 buckets) go into bins
+# of fixed capacity (mean + 8 standard deviations) instead of counted ones;
+# FLAG_TEST_SLACK halves the bins, so every such layer overflows and is sorted
+# and banded again with exact counts.  The structure must not change, and
+# plain builds of these sizes take the fixed-capacity path without a redo.
+SLACK_CASES = [
+    (9_000_000, 8, {}),
+    (8_700_001, 3, dict(partition_slots=24576, min_partition_slots=0)),
+    (9_500_000, 8, dict(threshold_mode=burr.THRESH_1PLUS)),
+]
+
+
+@pytest.mark.parametrize("n,r,params", SLACK_CASES)
+def test_sort_bin_overflow_is_sorted_again_exactly(n, r, params):
+    h, ref, keys, vals = _check_build(n, r, seed=n, flags=burr.FLAG_TEST_SLACK, **params)
+    plain = burr.build(keys, vals, r, **params)
+    assert h.export() == plain.export()
+    # the redo's kernels: the overflowing attempt and the exact one
+    assert h.stats()["kernel_launches"] > plain.stats()["kernel_launches"] + 6
 
 
 # Cut-point search (Sec. 3): cuts moved by the library's search kernel give
