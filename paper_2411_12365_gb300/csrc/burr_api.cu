@@ -380,17 +380,21 @@ constexpr int kJoinSlot = kBandSets + 1;
 constexpr int kFinalSlot = kBandSets + 2;
 constexpr int kSplitSlot = kBandSets + 3;
 constexpr int kSplitEndSlot = kBandSets + 4;
+constexpr int kCopySlot = kBandSets + 5;
+// Keys per chunk of host input copied ahead of the sort's first pass.
+constexpr uint64_t kStreamChunk = 1ull << 24;
 struct SideStream {
-    cudaStream_t main, side = nullptr, band2 = nullptr;
-    cudaEvent_t ev[kBandSets + 5] = {};
+    cudaStream_t main, side = nullptr, band2 = nullptr, copy = nullptr;
+    cudaEvent_t ev[kBandSets + 6] = {};
     explicit SideStream(cudaStream_t m) : main(m) {}
     cudaError_t init() {
         cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
         if (e == cudaSuccess && kBandSplitPct) e = cudaStreamCreateWithFlags(&band2, cudaStreamNonBlocking);
-        for (int i = 0; i < kBandSets + 5 && e == cudaSuccess; ++i)
+        for (int i = 0; i < kBandSets + 6 && e == cudaSuccess; ++i)
             e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
         return e;
     }
+    cudaError_t copy_init() { return copy ? cudaSuccess : cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking); }
     // `to` waits for everything enqueued so far on `from`
     cudaError_t order(cudaStream_t from, cudaStream_t to, int slot) {
         cudaError_t e = cudaEventRecord(ev[slot], from);
@@ -401,6 +405,11 @@ struct SideStream {
     // the main stream waits until band set `set` is no longer read (no-op if never used)
     cudaError_t reuse(int set) { return cudaStreamWaitEvent(main, ev[set], 0); }
     ~SideStream() {
+        if (copy) {
+            if (ev[kFinalSlot] && cudaEventRecord(ev[kFinalSlot], copy) == cudaSuccess)
+                cudaStreamWaitEvent(main, ev[kFinalSlot], 0);
+            cudaStreamDestroy(copy);
+        }
         if (band2) {
             if (ev[kFinalSlot] && cudaEventRecord(ev[kFinalSlot], band2) == cudaSuccess)
                 cudaStreamWaitEvent(main, ev[kFinalSlot], 0);
@@ -430,36 +439,42 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
     for (auto &row : tev)
         for (int &x : row) x = -1;
 
-    // inputs on the device
+    // Inputs on the device.  Where layer 0 uses the fixed-capacity sort, host
+    // inputs are copied in chunks on a stream of their own, and the sort's
+    // first pass takes each chunk as it arrives (the copy, at the host link's
+    // speed, takes several times the pass); otherwise they are copied here.
+    const uint64_t m0 = layer_slots(n, p.load_factor);
+    size_t slack0 = 0;
+    if (kSortSlack && n > 0 && m0 < (1ull << 32)) {
+        const uint64_t K0 = num_partitions(m0, layer_partition_slots(p, 0), p.min_partition_slots);
+        const LayerDesc L0 = make_desc(p, r, n, m0, layer_seed(p.seed, 0), K0, false, layer_partition_slots(p, 0));
+        slack0 = sort_slack_scratch_bytes(L0, vb);
+    }
+    const bool host_keys = !is_device_ptr(keys), host_vals = !is_device_ptr(values);
+    const bool stream_in = (host_keys || host_vals) && slack0 != 0 && p.layers > 0;
     const uint64_t *dkeys = keys;
     const void *dvals = values;
-    if (!is_device_ptr(keys)) {
+    if (host_keys) {
         void *d;
         CK(ar.alloc(&d, n * 8), "alloc keys");
-        CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy keys");
+        if (!stream_in) CK(cudaMemcpyAsync(d, keys, n * 8, cudaMemcpyHostToDevice, st), "copy keys");
         dkeys = (const uint64_t *)d;
     }
-    if (!is_device_ptr(values)) {
+    if (host_vals) {
         void *d;
         CK(ar.alloc(&d, n * vb), "alloc values");
-        CK(cudaMemcpyAsync(d, values, n * vb, cudaMemcpyHostToDevice, st), "copy values");
+        if (!stream_in) CK(cudaMemcpyAsync(d, values, n * vb, cudaMemcpyHostToDevice, st), "copy values");
         dvals = d;
     }
 
     // scratch sized for layer 0 (later layers and a normal base case are smaller)
-    const uint64_t m0 = layer_slots(n, p.load_factor);
     uint64_t cap_m = std::max<uint64_t>(m0, 64), cap_nb = num_buckets(cap_m, p.bucket_slots);
     void *sk, *sv, *bst, *ss, *cg, *yg, *bk[2], *bv[2], *ctr;
     CK(ar.alloc(&sk, n * 8), "alloc sorted keys");
     CK(ar.alloc(&sv, n * vb), "alloc sorted values");
     CK(ar.alloc(&bst, (cap_nb + 1) * 4), "alloc bucket offsets");
     // the exact sort's scratch, or the fixed-capacity sort's for layer 0 if larger
-    size_t ss_bytes = sort_scratch_bytes(n, cap_m, vb);
-    if (kSortSlack && n > 0 && m0 < (1ull << 32)) {
-        const uint64_t K0 = num_partitions(m0, layer_partition_slots(p, 0), p.min_partition_slots);
-        const LayerDesc L0 = make_desc(p, r, n, m0, layer_seed(p.seed, 0), K0, false, layer_partition_slots(p, 0));
-        ss_bytes = std::max(ss_bytes, sort_slack_scratch_bytes(L0, vb));
-    }
+    size_t ss_bytes = std::max(sort_scratch_bytes(n, cap_m, vb), slack0);
     CK(ar.alloc(&ss, ss_bytes), "alloc sort scratch");
     void *cgs[kBandSets] = {}, *ygs[kBandSets] = {};
     uint64_t cgcap[kBandSets] = {};
@@ -564,13 +579,36 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
         // (kErrSortSlack at the end of the layer), the layer is sorted and banded again exactly
         const size_t slack_bytes = kSortSlack ? sort_slack_scratch_bytes(L, vb) : 0;
         bool slack = slack_bytes != 0 && slack_bytes <= ss_bytes;
+        bool streamed = false;   // layer 0: the host inputs have been copied in
         unsigned long long hc[2] = {0, 0};
         uint32_t nflag = 0;
         for (;;) {
             tev[l][0] = tm.mark();
             if (slack) {
                 CK(launch_sort_slack_begin(L, vb, ss, st), "sort");
-                CK(launch_sort_slack_pass1(L, vb, cur_k, cur_v, 0, cur_n, ss, err, st), "sort");
+                if (l == 0 && stream_in && !streamed) {
+                    // host inputs: copy chunk c, then pass 1 over it, while chunk c+1 is copied
+                    CK(side.copy_init(), "copy stream");
+                    CK(side.order(st, side.copy, kCopySlot), "order");   // after the allocations
+                    for (uint64_t lo = 0; lo < n; lo += kStreamChunk) {
+                        const uint64_t hi = std::min<uint64_t>(n, lo + kStreamChunk);
+                        if (host_keys)
+                            CK(cudaMemcpyAsync((uint64_t *)dkeys + lo, keys + lo, (hi - lo) * 8,
+                                               cudaMemcpyHostToDevice, side.copy),
+                               "copy keys");
+                        if (host_vals)
+                            CK(cudaMemcpyAsync((char *)dvals + lo * vb, (const char *)values + lo * vb,
+                                               (hi - lo) * vb, cudaMemcpyHostToDevice, side.copy),
+                               "copy values");
+                        CK(side.order(side.copy, st, kCopySlot), "order");
+                        CK(launch_sort_slack_pass1(L, vb, cur_k, cur_v, lo, hi, ss, err, st), "sort");
+                        h->launches += 1;
+                    }
+                    h->launches -= 1;
+                    streamed = true;
+                } else {
+                    CK(launch_sort_slack_pass1(L, vb, cur_k, cur_v, 0, cur_n, ss, err, st), "sort");
+                }
                 CK(launch_sort_slack_end(L, vb, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");
             } else {
                 CK(launch_sort(L, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, ss, err, st), "sort");

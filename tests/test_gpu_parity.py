@@ -229,6 +229,21 @@ def test_sort_bin_overflow_is_sorted_again_exactly(n, r, params):
     assert h.stats()["kernel_launches"] > plain.stats()["kernel_launches"] + 6
 
 
+def test_host_inputs_streamed_into_the_sort():
+    """Host keys and values of a layer sorted with fixed-capacity bins are
+    copied in chunks of 2^24 keys, each taken by the sort's first pass as it
+    arrives: same structure as from device memory (3 chunks and a ragged one;
+    pinned and pageable host memory; keys on the host with values on the
+    device)."""
+    n, r = 3 * (1 << 24) + 12345, 8
+    keys, vals = _kv(n, r, seed=321)
+    want = burr.build(keys, vals, r).export()
+    hk, hv = keys.cpu(), vals.cpu()
+    assert burr.build(hk, hv, r).export() == want
+    assert burr.build(hk.pin_memory(), hv.pin_memory(), r).export() == want
+    assert burr.build(hk.pin_memory(), vals, r).export() == want
+
+
 # Cut-point search (Sec. 3): cuts moved by the library's search kernel give
 # the same structure as the oracle's search
 
