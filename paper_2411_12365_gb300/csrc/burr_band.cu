@@ -679,23 +679,20 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                 if (kExact) {
                     search = true;
                 } else {
+                    // the set [forced, B) was just found dependent: the threshold is the least
+                    // level above `forced` whose rows [level, B) insert, each candidate tried as
+                    // one set (rolled back if dependent).  Nearly always the first one inserts,
+                    // so this is one stream; inserting the bands [64, 128) and [32, 64) one
+                    // after the other took two.
                     code = 3;
-                    for (int k = 2; k >= 0; --k) {
-                        if (lv[k + 1] <= forced) break;
-                        // with every band above it kept, the band that reaches down to `forced`
-                        // completes the set [forced, B), which was just found dependent
-                        if (lv[k] <= forced) {
-                            code = (uint32_t)k + 1;
-                            break;
-                        }
-                        const int rc2 = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, lv[k], lv[k + 1], staged,
-                                                              lane);
+                    for (int k = 1; k <= 2; ++k) {
+                        if (lv[k] <= forced) continue;
+                        const int rc2 = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, lv[k], L.B, staged, lane);
                         if (rc2 == kOverflow) return;
-                        if (rc2 == kDependent) {
-                            code = (uint32_t)k + 1;
+                        if (rc2 == kOk) {
+                            code = (uint32_t)k;
                             break;
                         }
-                        code = (uint32_t)k;
                     }
                 }
             }
