@@ -765,8 +765,8 @@ template <typename V, int kG>
 __global__ void __launch_bounds__(32 * kBsWarps, kG >= 8 ? 4 : 1)
 k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z0,
                 BatchView bv, uint32_t R, uint32_t G, uint64_t njobs) {
-    __shared__ uint64_t sc[kBsWarps][kG][64];
-    __shared__ uint32_t sy[kBsWarps][kG][64];
+    __shared__ __align__(16) uint64_t sc[kBsWarps][kG][64];
+    __shared__ __align__(16) uint32_t sy[kBsWarps][kG][64];
     __shared__ uint64_t sbase[kBsWarps][kG];  // first slot of the group's structure in the layer arrays
     __shared__ uint64_t shi[kBsWarps][kG];    // one past the last block of the group's partition
     __shared__ uint32_t slen[kBsWarps][kG];   // its number of blocks
@@ -860,12 +860,15 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
             const uint32_t *yv = sy[warp][q];
 #pragma unroll 4
             for (int g = 15; g >= 0; --g) {
-                const int i = 4 * g + 3;
-                const uint64_t c0 = c[i], c1 = c[i - 1], c2 = c[i - 2], c3 = c[i - 3];
-                const uint32_t a0 = ((yv[i] >> k) & 1u) ^ parity64(c0 & T);
-                const uint32_t a1 = ((yv[i - 1] >> k) & 1u) ^ parity64((c1 >> 1) & T);
-                const uint32_t a2 = ((yv[i - 2] >> k) & 1u) ^ parity64((c2 >> 2) & T);
-                const uint32_t a3 = ((yv[i - 3] >> k) & 1u) ^ parity64((c3 >> 3) & T);
+                // slots 4g .. 4g+3 in three 16-byte shared reads
+                const ulonglong2 clo = *reinterpret_cast<const ulonglong2 *>(c + 4 * g);
+                const ulonglong2 chi = *reinterpret_cast<const ulonglong2 *>(c + 4 * g + 2);
+                const uint4 yq = *reinterpret_cast<const uint4 *>(yv + 4 * g);
+                const uint64_t c0 = chi.y, c1 = chi.x, c2 = clo.y, c3 = clo.x;
+                const uint32_t a0 = ((yq.w >> k) & 1u) ^ parity64(c0 & T);
+                const uint32_t a1 = ((yq.z >> k) & 1u) ^ parity64((c1 >> 1) & T);
+                const uint32_t a2 = ((yq.y >> k) & 1u) ^ parity64((c2 >> 2) & T);
+                const uint32_t a3 = ((yq.x >> k) & 1u) ^ parity64((c3 >> 3) & T);
                 const uint32_t l1 = (uint32_t)c1, l2 = (uint32_t)c2, l3 = (uint32_t)c3;
                 const uint32_t z0 = a0;
                 const uint32_t z1 = a1 ^ (l1 & z0);
