@@ -4,6 +4,7 @@
 // burr_sort.cu, burr_band.cu and burr_query.cu; this file only sizes layers,
 // allocates, launches and reads back one counter per layer.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -876,6 +877,8 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
     keep_pool_memory();
     Arena ar(st);
     Timer tm((p.flags & BURR_FLAG_TIMING) != 0, st);
+    SideStream side(st);   // back-substitution beside the next layer, as in build_impl
+    CK(side.init(), "side stream");
     const int t_begin = tm.mark();
 
     const uint64_t *dkeys = keys;
@@ -903,9 +906,23 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
     unsigned long long *bcount = (unsigned long long *)ctr;
     uint32_t *ffail = (uint32_t *)((char *)ctr + (size_t)S * 8);
     uint32_t *err = ffail + S;
-    // buffers sized by the largest layer seen so far
-    void *scratch = nullptr, *bst = nullptr, *cg = nullptr, *yg = nullptr;
-    uint64_t cap_scratch = 0, cap_nb = 0, cap_slots = 0;
+    // buffers sized by the largest layer seen so far; the band arrays rotate over
+    // kBandSets sets (a layer's back-substitution may still read its set while
+    // the next layers band)
+    void *scratch = nullptr, *bst = nullptr;
+    void *cgs[kBandSets] = {}, *ygs[kBandSets] = {};
+    uint64_t cap_scratch = 0, cap_nb = 0, cgcap[kBandSets] = {};
+    auto ensure_band = [&](int set, uint64_t slots) -> int {
+        if (slots > cgcap[set]) {
+            CK(side.reuse(set), "order");   // its previous user's back-substitution is done
+            if (cgs[set]) ar.release(cgs[set]);
+            if (ygs[set]) ar.release(ygs[set]);
+            CK(ar.alloc(&cgs[set], slots * 8), "alloc band");
+            CK(ar.alloc(&ygs[set], slots * vb), "alloc band values");
+            cgcap[set] = slots;
+        }
+        return BURR_OK;
+    };
     auto ensure = [&](const BatchTables &T) -> int {
         const size_t need = sort_batch_scratch_bytes(T.nkeys, T.ngroups, vb);
         if (need > cap_scratch) {
@@ -918,14 +935,29 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             CK(ar.alloc(&bst, (T.nbuckets + 1) * 4), "alloc bucket offsets");
             cap_nb = T.nbuckets + 1;
         }
-        if (T.slots > cap_slots) {
-            if (cg) ar.release(cg);
-            if (yg) ar.release(yg);
-            CK(ar.alloc(&cg, T.slots * 8), "alloc band");
-            CK(ar.alloc(&yg, T.slots * vb), "alloc band values");
-            cap_slots = T.slots;
-        }
         return BURR_OK;
+    };
+    // a bumping layer's back-substitution, queued on the side stream after the next layer's sort;
+    // bsm[l]: event marks of layer l's back-substitution launches (a split band's first one, the rest)
+    struct PendingBatchBacksub {
+        bool on = false;
+        uint32_t l = 0;
+        int set = 0;
+        BatchView v;
+        uint64_t *z = nullptr;
+    } pending;
+    std::vector<std::array<int, 4>> bsm(p.layers + 1, std::array<int, 4>{-1, -1, -1, -1});
+    auto start_backsub = [&]() -> cudaError_t {
+        if (!pending.on) return cudaSuccess;
+        pending.on = false;
+        cudaError_t e = side.order(st, side.side, kOrderSlot);
+        if (e != cudaSuccess) return e;
+        bsm[pending.l][2] = tm.mark_on(side.side);
+        e = launch_backsub(LayerDesc(), vb, (const uint64_t *)cgs[pending.set], ygs[pending.set], pending.z, side.side,
+                           &pending.v);
+        if (e != cudaSuccess) return e;
+        bsm[pending.l][3] = tm.mark_on(side.side);
+        return side.solved(pending.set);
     };
     auto view = [&](const BatchTables &T, BatchView &v) -> int {
         StructDesc *dsd;
@@ -993,6 +1025,10 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         }
         BatchView v;
         if ((rc = view(T, v))) return rc;
+        const int set = (int)(l % kBandSets);
+        if ((rc = ensure_band(set, T.slots))) return rc;
+        CK(side.reuse(set), "order");   // the set's last back-substitution is done
+        void *cg = cgs[set], *yg = ygs[set];
         uint64_t *th = nullptr, *z, *tflags = nullptr;
         uint32_t *tdir = nullptr;
         uint8_t *tex = nullptr;
@@ -1021,6 +1057,7 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         const int w = (int)(l & 1);
         const int t0 = tm.mark();
         CK(launch_sort_batch(v, vb, cur_k, cur_v, (uint64_t *)sk, sv, (uint32_t *)bst, scratch, st), "sort");
+        CK(start_backsub(), "backsub");   // the previous layer's, now that this layer's sort is queued
         if (search) {
             CK(launch_cut_search(none, (const uint64_t *)sk, (const uint32_t *)bst, p.cut_search,
                                  p.cut_search_range, nullptr, st, &v),
@@ -1028,8 +1065,31 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             for (auto *h : hs) h->launches += 1;
         }
         const int t1 = tm.mark();
-        CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
-                       (uint64_t *)bk[w], bv2[w], bcount, err, st, &v), "band");
+        // partitions in the order table (longest first): the first 90% in one launch, the rest in a
+        // second launch on its own stream, and the first launch's back-substitution right after it
+        const uint32_t K1 = kBandSplitPct && v.nparts >= 4096 ? (uint32_t)((uint64_t)v.nparts * kBandSplitPct / 100)
+                                                              : 0;
+        BatchView vrest = v;
+        if (K1 > 0 && K1 < v.nparts && v.part_order) {
+            BatchView va = v;
+            va.nparts = K1;
+            vrest.part_order = v.part_order + K1;
+            vrest.nparts = v.nparts - K1;
+            CK(side.order(st, side.band2, kSplitSlot), "order");
+            CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
+                           (uint64_t *)bk[w], bv2[w], bcount, err, st, &va), "band");
+            CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
+                           (uint64_t *)bk[w], bv2[w], bcount, err, side.band2, &vrest), "band");
+            CK(side.order(st, side.side, kOrderSlot), "order");
+            bsm[l][0] = tm.mark_on(side.side);
+            CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, side.side, &va), "backsub");
+            bsm[l][1] = tm.mark_on(side.side);
+            CK(side.order(side.band2, st, kSplitEndSlot), "order");
+            for (auto *h : hs) h->launches += 2;
+        } else {
+            CK(launch_band(none, vb, (const uint64_t *)sk, sv, (const uint32_t *)bst, (uint64_t *)cg, yg, th, tex,
+                           (uint64_t *)bk[w], bv2[w], bcount, err, st, &v), "band");
+        }
         const int t2 = tm.mark();
         ThreshSeg *dsegs = nullptr;
         uint32_t *dblk = nullptr, *tcounts = nullptr;
@@ -1039,8 +1099,11 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             CK(ar.alloc((void **)&tcounts, std::max<size_t>(blkseg.size(), 1) * 4), "alloc threshold counts");
             CK(launch_thresh_flags(tex, dsegs, dblk, (uint32_t)blkseg.size(), tflags, tcounts, tdir, st), "flags");
         }
-        CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
-        const int t3 = tm.mark();
+        pending.on = true;
+        pending.l = l;
+        pending.set = set;
+        pending.v = vrest;
+        pending.z = z;
         for (auto *h : hs) h->launches += 6;
         std::vector<unsigned long long> cnt(who.size());
         std::vector<uint32_t> hdir(onep ? blkseg.size() + 1 : 0);
@@ -1079,28 +1142,32 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             }
             Ls.z = z + D.z_base;
             hs[s]->stage_ms[l][0] = tm.ms(t0, t1);
-            hs[s]->stage_ms[l][1] = tm.ms(t1, t2);
-            hs[s]->stage_ms[l][2] = tm.ms(t2, t3);
+            hs[s]->stage_ms[l][1] = tm.ms(t1, t2);   // [l][2] once the build's events are all recorded
             n[s] = cnt[i];
         }
         cur_k = (const uint64_t *)bk[w];
         cur_v = bv2[w];
     }
+    CK(start_backsub(), "backsub");   // the last bumping layer's
     // base case of every structure with keys left; retries per structure
-    std::vector<uint32_t> attempt(S, 0), pending;
+    std::vector<uint32_t> attempt(S, 0), left;
     for (uint32_t s = 0; s < S; ++s) {
         hs[s]->L[p.layers].n = n[s];
         hs[s]->L[p.layers].seed_index = p.layers;
-        if (n[s]) pending.push_back(s);
+        if (n[s]) left.push_back(s);
     }
     const int wfb = (int)(p.layers & 1);
-    while (!pending.empty()) {
+    while (!left.empty()) {
         BatchTables T;
-        int rc = batch_tables(p, r, offsets, n, pending, p.layers, &attempt, T);
+        int rc = batch_tables(p, r, offsets, n, left, p.layers, &attempt, T);
         if (rc) return rc;
         if ((rc = ensure(T))) return rc;
         BatchView v;
         if ((rc = view(T, v))) return rc;
+        const int set = (int)(p.layers % kBandSets);
+        if ((rc = ensure_band(set, T.slots))) return rc;
+        CK(side.reuse(set), "order");
+        void *cg = cgs[set], *yg = ygs[set];
         uint64_t *z;
         CK(table_alloc(T.zw * 8, &z), "alloc tables");
         CK(cudaMemsetAsync(ctr, 0, (size_t)S * 12 + 64, st), "clear counters");
@@ -1109,15 +1176,15 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
                        (uint64_t *)bk[wfb], bv2[wfb], bcount, err, st, &v), "band");
         CK(launch_backsub(none, vb, (const uint64_t *)cg, yg, z, st, &v), "backsub");
         for (auto *h : hs) h->launches += 6;
-        std::vector<uint32_t> f(pending.size());
+        std::vector<uint32_t> f(left.size());
         uint32_t e = 0;
         CK(cudaMemcpyAsync(f.data(), ffail, f.size() * 4, cudaMemcpyDeviceToHost, st), "read flags");
         CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
         CK(cudaStreamSynchronize(st), "base case");
         if (e) return fail(BURR_ERR_INTERNAL, "base case: device error 0x%x", e);
         std::vector<uint32_t> again;
-        for (uint32_t i = 0; i < pending.size(); ++i) {
-            const uint32_t s = pending[i];
+        for (uint32_t i = 0; i < left.size(); ++i) {
+            const uint32_t s = left[i];
             const StructDesc &D = T.sd[i];
             if (f[i] & kErrUnsolvable) {
                 if (++attempt[s] > p.fallback_max_retries)
@@ -1135,12 +1202,18 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
             F.z = z + D.z_base;
             hs[s]->fb_attempt = attempt[s];
         }
-        pending.swap(again);
+        left.swap(again);
     }
+    CK(side.order(side.side, st, kJoinSlot), "order");
     const int t_end = tm.mark();
     CK(cudaStreamSynchronize(st), "build");
     const float total = tm.ms(t_begin, t_end);
-    for (auto *h : hs) h->total_ms = total;
+    for (auto *h : hs) {
+        h->total_ms = total;
+        for (uint32_t l = 0; l < p.layers; ++l)
+            if (h->L[l].n)
+                h->stage_ms[l][2] = tm.ms(bsm[l][0], bsm[l][1]) + tm.ms(bsm[l][2], bsm[l][3]);
+    }
     return BURR_OK;
 }
 
