@@ -82,7 +82,8 @@ struct alignas(16) StagedRow {
 // threshold mode: more read-ahead means fewer steps but more instructions per
 // step, and with many warps per SM competing for issue slots two measured
 // best in both modes (10^8 keys, r=8; 1+-bit: 1, 2, 3, 4 slots gave 27.2,
-// 26.6, 27.5, 27.6 ms per build and query step).
+// 26.6, 27.5, 27.6 ms per build and query step; 2-bit, layer-0 band of 10^9
+// keys: 68.2, 65.9, 69.0, 80.1 ms).
 #ifndef BURR_BAND_LOOKAHEAD_2BIT
 #define BURR_BAND_LOOKAHEAD_2BIT 2
 #endif
