@@ -762,7 +762,12 @@ constexpr int kBsGroups = 8;
 // job is one set of G partitions; the grid may hold fewer warps than jobs
 // (a cap on the CTAs per SM leaves room beside it for the next layer's
 // kernels), and then every warp walks the jobs with the grid's stride.
-template <typename V, int kG>
+//
+// kPL bit planes per lane (1, 2 or 4; for r up to 8, 16, 32): lane k of a
+// group solves planes k*kPL .. k*kPL + kPL - 1, each with its own window T, and
+// the rows' reads, shifts and low bits serve all of them.  At r = 16 a group
+// then needs 8 lanes instead of 16, so a warp takes 4 partitions instead of 2.
+template <typename V, int kG, int kPL>
 __global__ void __launch_bounds__(32 * kBsWarps, kG >= 8 ? 4 : 1)
 k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restrict__ Yg, uint64_t *__restrict__ Z0,
                 BatchView bv, uint32_t R, uint32_t G, uint64_t njobs) {
@@ -832,8 +837,10 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
             ny1[g] = Yg[s0 + lane + 32];
         }
     }
-    const bool solve = k < r;
-    uint64_t T = 0;
+    const bool solve = k * kPL < r;
+    uint64_t T[kPL];
+#pragma unroll
+    for (int pl = 0; pl < kPL; ++pl) T[pl] = 0;
     for (uint32_t t = 0; t < maxlen; ++t) {
         __syncwarp();
 #pragma unroll
@@ -865,19 +872,25 @@ k_backsub_multi(LayerDesc L0, const uint64_t *__restrict__ Cg, const V *__restri
                 const ulonglong2 clo = *reinterpret_cast<const ulonglong2 *>(c + 4 * g);
                 const ulonglong2 chi = *reinterpret_cast<const ulonglong2 *>(c + 4 * g + 2);
                 const uint4 yq = *reinterpret_cast<const uint4 *>(yv + 4 * g);
-                const uint64_t c0 = chi.y, c1 = chi.x, c2 = clo.y, c3 = clo.x;
-                const uint32_t a0 = ((yq.w >> k) & 1u) ^ parity64(c0 & T);
-                const uint32_t a1 = ((yq.z >> k) & 1u) ^ parity64((c1 >> 1) & T);
-                const uint32_t a2 = ((yq.y >> k) & 1u) ^ parity64((c2 >> 2) & T);
-                const uint32_t a3 = ((yq.x >> k) & 1u) ^ parity64((c3 >> 3) & T);
-                const uint32_t l1 = (uint32_t)c1, l2 = (uint32_t)c2, l3 = (uint32_t)c3;
-                const uint32_t z0 = a0;
-                const uint32_t z1 = a1 ^ (l1 & z0);
-                const uint32_t z2 = a2 ^ ((l2 >> 1) & z0) ^ (l2 & z1);
-                const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
-                T = (T << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
+                const uint64_t c0 = chi.y, c1 = chi.x >> 1, c2 = clo.y >> 2, c3 = clo.x >> 3;
+                const uint32_t l1 = (uint32_t)chi.x, l2 = (uint32_t)clo.y, l3 = (uint32_t)clo.x;
+#pragma unroll
+                for (int pl = 0; pl < kPL; ++pl) {
+                    const uint32_t b = k * kPL + (uint32_t)pl;   // this plane's value bit
+                    const uint32_t a0 = ((yq.w >> b) & 1u) ^ parity64(c0 & T[pl]);
+                    const uint32_t a1 = ((yq.z >> b) & 1u) ^ parity64(c1 & T[pl]);
+                    const uint32_t a2 = ((yq.y >> b) & 1u) ^ parity64(c2 & T[pl]);
+                    const uint32_t a3 = ((yq.x >> b) & 1u) ^ parity64(c3 & T[pl]);
+                    const uint32_t z0 = a0;
+                    const uint32_t z1 = a1 ^ (l1 & z0);
+                    const uint32_t z2 = a2 ^ ((l2 >> 1) & z0) ^ (l2 & z1);
+                    const uint32_t z3 = a3 ^ ((l3 >> 2) & z0) ^ ((l3 >> 1) & z1) ^ (l3 & z2);
+                    T[pl] = (T[pl] << 4) | (uint64_t)(((z0 << 3) | (z1 << 2) | (z2 << 1) | z3) & 15u);
+                }
             }
-            Z[(bhi - 1 - t) * r + k] = T;
+#pragma unroll
+            for (int pl = 0; pl < kPL; ++pl)
+                if (k * kPL + (uint32_t)pl < r) Z[(bhi - 1 - t) * r + k * kPL + pl] = T[pl];
         }
     }
     __syncwarp();   // the warp's shared arrays are reused by its next job
@@ -936,30 +949,41 @@ cudaError_t launch_band(const LayerDesc &L, uint32_t vbytes, const uint64_t *key
     }
 }
 
-template <typename V, int kG>
+template <typename V, int kG, int kPL>
 cudaError_t backsub_launch(const LayerDesc &L, const uint64_t *Cg, const V *Yg, uint64_t *Z, cudaStream_t st,
                            const BatchView &v, uint32_t R, uint32_t G, uint64_t njobs, unsigned grid) {
-    const cudaError_t e = prefer_shared(k_backsub_multi<V, kG>);
+    const cudaError_t e = prefer_shared(k_backsub_multi<V, kG, kPL>);
     if (e != cudaSuccess) return e;
-    k_backsub_multi<V, kG><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, Yg, Z, v, R, G, njobs);
+    k_backsub_multi<V, kG, kPL><<<grid, 32 * kBsWarps, 0, st>>>(L, Cg, Yg, Z, v, R, G, njobs);
     return cudaGetLastError();
+}
+
+// Planes per lane: one for values of a byte (r <= 8 lanes already fit four
+// groups in a warp), else as many as the value's bytes.
+template <typename V>
+constexpr int planes_per_lane() {
+    return sizeof(V) == 1 ? 1 : (int)sizeof(V);
 }
 
 template <typename V>
 cudaError_t backsub_impl(const LayerDesc &L, const uint64_t *Cg, const V *Yg, uint64_t *Z, cudaStream_t st,
                          const BatchView &v, uint32_t R, uint32_t G, uint64_t njobs, unsigned grid) {
-    if (G <= 1) return backsub_launch<V, 1>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
-    if (G <= 2) return backsub_launch<V, 2>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
-    if (G <= 4) return backsub_launch<V, 4>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
-    return backsub_launch<V, kBsGroups>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    constexpr int PL = planes_per_lane<V>();
+    if (G <= 1) return backsub_launch<V, 1, PL>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    if (G <= 2) return backsub_launch<V, 2, PL>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    if (G <= 4) return backsub_launch<V, 4, PL>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
+    return backsub_launch<V, kBsGroups, PL>(L, Cg, Yg, Z, st, v, R, G, njobs, grid);
 }
 
 cudaError_t launch_backsub(const LayerDesc &L, uint32_t vbytes, const uint64_t *Cg, const void *Yg,
                            uint64_t *Z, cudaStream_t st, const BatchView *bv, uint32_t max_ctas_per_sm) {
     const uint64_t parts = bv ? bv->nparts : (part_end(L) > L.part_lo ? part_end(L) - L.part_lo : 0);
     if (parts == 0) return cudaSuccess;
-    // several partitions per warp; a batch's structures may differ in r (up to 8 bits per value byte)
-    const uint32_t R = bv ? 8u * vbytes : L.r;
+    // several partitions per warp; a batch's structures may differ in r (up to 8 bits per value
+    // byte); R lanes per partition, each solving one bit plane for one-byte values, else as many
+    // planes as the value has bytes
+    const uint32_t pl = vbytes == 1 ? 1u : vbytes;
+    const uint32_t R = bv ? 8u * vbytes / pl : (L.r + pl - 1) / pl;
     const uint32_t G = std::min<uint32_t>(32u / R, (uint32_t)kBsGroups);
     const uint64_t njobs = (parts + G - 1) / G;
     uint64_t grid = (njobs + kBsWarps - 1) / kBsWarps;
