@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
 }
 
 // Back-substitution, right to left over the partition's owned slots, one
-// lane per value bit: Z[i] = Y[i] ^ parity((C[i] >> 1) & Z[i+1 .. i+63]),
+// window per value bit: Z[i] = Y[i] ^ parity((C[i] >> 1) & Z[i+1 .. i+63]),
 // Z[i] = 0 on empty slots (C = Y = 0 there).  The 64-bit register T holds Z of
 // the 64 slots right of the current group (bit j = slot i+1+j); after a block
 // of 64 slots it is exactly that block's table word for this bit plane.
@@ -745,11 +745,11 @@ __device__ __forceinline__ uint32_t parity64(uint64_t x) {
 }
 
 // Back-substitution with several partitions per warp: a partition needs only
-// r lanes (one per bit plane), so a warp solves G = min(32 / R, kBsGroups)
-// partitions side by side, lanes [q*R, q*R + R) on partition q, where R is an
-// upper bound of r over the launch (r itself for one structure, 8 x value bytes
-// for a batch, whose structures may differ in r; lanes past a structure's r
-// sit out).  Each group runs the four-slot steps above; sharing each instruction
+// R lanes (R = r for one-byte values, one bit plane per lane; r / 2 or r / 4
+// rounded up with 2 or 4 planes per lane for wider values), so a warp solves
+// G = min(32 / R, kBsGroups) partitions side by side, lanes [q*R, q*R + R) on
+// partition q.  For a batch, whose structures may differ in r, R comes from
+// the widest value type (8 lanes); lanes past a structure's r sit out.  Each group runs the four-slot steps above; sharing each instruction
 // among G partitions cuts the issue load G-fold, which matters because the
 // solve runs beside the next layer's sort and band.  Partitions of one warp may
 // differ in length: each walks its own blocks from the right, and a finished
