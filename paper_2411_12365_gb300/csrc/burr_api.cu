@@ -802,13 +802,29 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
                  const std::vector<uint32_t> *fb_attempt, BatchTables &T) {
     T = BatchTables();
     T.who = who;
+    const bool fb = fb_attempt != nullptr;
+    const uint64_t Pl = layer_partition_slots(p, l);
+    {
+        // sizes of the tables first (for 10^4 structures they hold ~10^6 entries)
+        uint64_t np = 0, ng = 0, nt = 0;
+        for (const uint32_t s : who) {
+            const uint64_t m = fb ? fallback_slots(n[s], p.fallback_slack, (*fb_attempt)[s])
+                                  : layer_slots(n[s], p.load_factor);
+            np += fb ? 1 : num_partitions(m, Pl, p.min_partition_slots);
+            ng += (num_buckets(m, p.bucket_slots) + 63) / 64;
+            nt += (n[s] + kSortTile - 1) / kSortTile;
+        }
+        T.sd.reserve(who.size());
+        T.part_struct.reserve(np);
+        T.group_struct.reserve(ng);
+        T.tile_struct.reserve(nt);
+        T.tile_lo.reserve(nt);
+    }
     for (uint32_t i = 0; i < who.size(); ++i) {
         const uint32_t s = who[i];
-        const bool fb = fb_attempt != nullptr;
         const uint64_t m = fb ? fallback_slots(n[s], p.fallback_slack, (*fb_attempt)[s])
                               : layer_slots(n[s], p.load_factor);
         if (m >= (1ull << 32)) return fail(BURR_ERR_INVALID, "structure %u needs >= 2^32 slots", s);
-        const uint64_t Pl = layer_partition_slots(p, l);
         const uint64_t K = fb ? 1 : num_partitions(m, Pl, p.min_partition_slots);
         const uint64_t sigma = layer_seed(p.seed, fb ? p.layers + (*fb_attempt)[s] : l);
         StructDesc D;
@@ -829,12 +845,10 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
         D.part_base = (uint32_t)T.nparts;
         D.ngroups = (uint32_t)ng;
         T.sd.push_back(D);
-        for (uint64_t k = 0; k < K; ++k) T.part_struct.push_back(i);
-        for (uint64_t g = 0; g < ng; ++g) T.group_struct.push_back(i);
-        for (uint64_t t = 0; t < n[s]; t += kSortTile) {
-            T.tile_struct.push_back(i);
-            T.tile_lo.push_back(offsets[s] + t);
-        }
+        T.part_struct.insert(T.part_struct.end(), K, i);
+        T.group_struct.insert(T.group_struct.end(), ng, i);
+        T.tile_struct.insert(T.tile_struct.end(), (n[s] + kSortTile - 1) / kSortTile, i);
+        for (uint64_t t = 0; t < n[s]; t += kSortTile) T.tile_lo.push_back(offsets[s] + t);
         T.nbuckets += D.L.nb;
         T.ngroups += ng;
         T.nparts += K;
@@ -846,14 +860,21 @@ int batch_tables(const burr_params &p, const std::vector<uint32_t> &r, const std
     }
     // Longest partitions first: a warp's partition is one dependent chain, so
     // the launch ends with the short ones instead of a long one started late.
-    std::vector<uint64_t> len(T.nparts);
+    // (A counting sort on the length in buckets, stable like the comparison
+    // sort it replaces: most partitions share a handful of lengths.)
+    std::vector<uint32_t> len(T.nparts);
+    uint32_t lmax = 0;
     for (uint32_t i = 0; i < T.sd.size(); ++i)
-        for (uint64_t k = 0; k < T.sd[i].L.K; ++k)
-            len[T.sd[i].part_base + k] = part_bucket(T.sd[i].L, k + 1) - part_bucket(T.sd[i].L, k);
+        for (uint64_t k = 0; k < T.sd[i].L.K; ++k) {
+            const uint32_t x = (uint32_t)(part_bucket(T.sd[i].L, k + 1) - part_bucket(T.sd[i].L, k));
+            len[T.sd[i].part_base + k] = x;
+            lmax = std::max(lmax, x);
+        }
+    std::vector<uint32_t> at(lmax + 2, 0);
+    for (const uint32_t x : len) ++at[lmax - x + 1];   // decreasing length
+    for (uint32_t x = 1; x <= lmax + 1; ++x) at[x] += at[x - 1];
     T.part_order.resize(T.nparts);
-    for (uint32_t j = 0; j < T.nparts; ++j) T.part_order[j] = j;
-    std::stable_sort(T.part_order.begin(), T.part_order.end(),
-                     [&](uint32_t a, uint32_t b) { return len[a] > len[b]; });
+    for (uint32_t j = 0; j < T.nparts; ++j) T.part_order[at[lmax - len[j]]++] = j;
     return BURR_OK;
 }
 
