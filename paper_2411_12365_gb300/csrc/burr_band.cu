@@ -243,10 +243,10 @@ __device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, un
 }
 
 // Plain 128-bit read of a ring slot.  A slot goes from empty to its final
-// contents once per set (one atomic write), so a read that sees a nonzero row
-// and a valid right-hand side has seen a stored equation that stays; any
-// other result (empty, or a torn read of a slot being written) is treated as
-// "not known to be occupied".
+// contents once per set (one atomic write of row and right-hand side), and a
+// step's reads are issued only after the previous step's swaps have returned
+// (their addresses depend on them), so a read sees a slot either empty (all
+// zero) or with both words of a stored equation that stays.
 __device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, unsigned long long &y) {
     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c), "=l"(y) : "r"(addr) : "memory");
 }
@@ -334,25 +334,26 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         uint32_t over = 0;
         uint32_t y2 = (uint32_t)y ^ (uint32_t)oy;   // right-hand sides fit in 32 bits
         uint32_t yh = kTag ? (uint32_t)(y >> 32) ^ (uint32_t)(oy >> 32) : 0u;   // tags (bits 1..)
-        bool go = true;
-        bool use[kLook > 0 ? kLook : 1];
+        // while go is 1, bits 0 .. j-1 are clear, so bit j is the leading bit if set; a stored row
+        // has its pivot bit (bit 0) set.  Decisions as 0/1 words and all-ones masks: measured
+        // 5.7% fewer instructions than with predicates and selects (layer-0 band 65.8 -> 63.9 ms
+        // at 10^9 keys).
+        uint32_t go = 1u;
+        uint32_t um[kLook > 0 ? kLook : 1];   // 0 or all ones: the read-ahead row of slot pos+j is used
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
-            // while go holds, bits 0 .. j-1 are clear, so bit j is the leading bit if set; a stored
-            // row has its pivot bit (bit 0) set and its right-hand side marked valid
-            const bool occ = ((uint32_t)lc[j - 1] & (uint32_t)(ly[j - 1] >> 32) & 1u) != 0u;
-            const bool bit = (lo32 >> j) & 1u;
-            use[j - 1] = go && bit && occ;
-            lo32 ^= use[j - 1] ? (uint32_t)lc[j - 1] << j : 0u;
-            go = go && (!bit || occ);
+            const uint32_t occ = (uint32_t)lc[j - 1] & 1u;
+            const uint32_t bit = (lo32 >> j) & 1u;
+            um[j - 1] = 0u - (go & bit & occ);
+            lo32 ^= ((uint32_t)lc[j - 1] << j) & um[j - 1];
+            go &= (bit ^ 1u) | occ;
         }
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
-            const unsigned long long sh = lc[j - 1] << j;
-            hi32 ^= use[j - 1] ? (uint32_t)(sh >> 32) : 0u;
-            over ^= use[j - 1] ? (uint32_t)(lc[j - 1] >> (64 - j)) : 0u;
-            y2 ^= use[j - 1] ? (uint32_t)ly[j - 1] : 0u;
-            if (kTag) yh ^= use[j - 1] ? (uint32_t)(ly[j - 1] >> 32) : 0u;
+            hi32 ^= (uint32_t)((lc[j - 1] << j) >> 32) & um[j - 1];
+            over ^= (uint32_t)(lc[j - 1] >> (64 - j)) & um[j - 1];
+            y2 ^= (uint32_t)ly[j - 1] & um[j - 1];
+            if (kTag) yh ^= (uint32_t)(ly[j - 1] >> 32) & um[j - 1];
         }
         // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0; it is
         // almost always in the low word
