@@ -242,13 +242,26 @@ __device__ __forceinline__ void slot_cas(unsigned addr, unsigned long long c, un
                  : "memory");
 }
 
-// Plain 128-bit read of a ring slot.  A slot goes from empty to its final
-// contents once per set (one atomic write of row and right-hand side), and a
-// step's reads are issued only after the previous step's swaps have returned
-// (their addresses depend on them), so a read sees a slot either empty (all
-// zero) or with both words of a stored equation that stays.
-__device__ __forceinline__ void slot_load(unsigned addr, unsigned long long &c, unsigned long long &y) {
-    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c), "=l"(y) : "r"(addr) : "memory");
+// Plain read of a ring slot, as 32-bit words: the row's two halves and the
+// low word of the right-hand side; the right-hand side's high word (the tags
+// of a tagged set) only when kHi (a sink otherwise, so it takes no register).
+// A slot goes from empty to its final contents once per set (one atomic write
+// of row and right-hand side), and a step's reads are issued only after the
+// previous step's swaps have returned (their addresses depend on them), so a
+// read sees a slot either empty (all zero) or with both words of a stored
+// equation that stays.
+template <bool kHi>
+__device__ __forceinline__ void slot_load_words(unsigned addr, uint32_t &clo, uint32_t &chi, uint32_t &ylo,
+                                                uint32_t &yhi) {
+    if (kHi) {
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(clo), "=r"(chi), "=r"(ylo), "=r"(yhi)
+                     : "r"(addr)
+                     : "memory");
+    } else {
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, _}, [%3];" : "=r"(clo), "=r"(chi), "=r"(ylo) : "r"(addr) : "memory");
+        yhi = 0u;
+    }
 }
 
 // Stream staged rows [lo, hi) (index range) into the band; stored ring
@@ -302,9 +315,11 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         // ahead are inside the window; past the ring's end they are the zero pad, which reads
         // as empty (the step then ends there, and the next swap goes to the true slot).
         unsigned long long oc, oy;
-        unsigned long long lc[kLook > 0 ? kLook : 1], ly[kLook > 0 ? kLook : 1];
+        uint32_t lcl[kLook > 0 ? kLook : 1], lch[kLook > 0 ? kLook : 1], lyl[kLook > 0 ? kLook : 1],
+            lyh[kLook > 0 ? kLook : 1];
 #pragma unroll
-        for (int j = 0; j < kLook; ++j) slot_load(addr + (unsigned)((j + 1) * sizeof(RingSlot)), lc[j], ly[j]);
+        for (int j = 0; j < kLook; ++j)
+            slot_load_words<kTag>(addr + (unsigned)((j + 1) * sizeof(RingSlot)), lcl[j], lch[j], lyl[j], lyh[j]);
         slot_cas(addr, cur, y, oc, oy);
         // an empty slot is all zero and a stored row has its pivot bit set
         const bool stored = has && ((uint32_t)oc & 1u) == 0u;
@@ -342,18 +357,18 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
         uint32_t um[kLook > 0 ? kLook : 1];   // 0 or all ones: the read-ahead row of slot pos+j is used
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
-            const uint32_t occ = (uint32_t)lc[j - 1] & 1u;
+            const uint32_t occ = lcl[j - 1] & 1u;
             const uint32_t bit = (lo32 >> j) & 1u;
             um[j - 1] = 0u - (go & bit & occ);
-            lo32 ^= ((uint32_t)lc[j - 1] << j) & um[j - 1];
+            lo32 ^= (lcl[j - 1] << j) & um[j - 1];
             go &= (bit ^ 1u) | occ;
         }
 #pragma unroll
         for (int j = 1; j <= kLook; ++j) {
-            hi32 ^= (uint32_t)((lc[j - 1] << j) >> 32) & um[j - 1];
-            over ^= (uint32_t)(lc[j - 1] >> (64 - j)) & um[j - 1];
-            y2 ^= (uint32_t)ly[j - 1] & um[j - 1];
-            if (kTag) yh ^= (uint32_t)(ly[j - 1] >> 32) & um[j - 1];
+            hi32 ^= __funnelshift_l(lcl[j - 1], lch[j - 1], (unsigned)j) & um[j - 1];
+            over ^= (lch[j - 1] >> (32 - j)) & um[j - 1];
+            y2 ^= lyl[j - 1] & um[j - 1];
+            if (kTag) yh ^= lyh[j - 1] & um[j - 1];
         }
         // normalise: shift the leading bit (>= 1 for an active lane) down to bit 0; it is
         // almost always in the low word
