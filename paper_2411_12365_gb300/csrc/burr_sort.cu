@@ -385,10 +385,11 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
             if (d < D && hist[d]) res[k] = atomicAdd(&cursor[(uint64_t)seg * (SEG ? D : 0) + d], hist[d]);
         }
         block_scan(hist, excl, D, warp_sums);
+        // gbase[d] - excl[d]: the output of tile index i is gbase[d] + i, one shared read per key
 #pragma unroll
         for (int k = 0; k < (int)(kMaxDigits / kTileThreads); ++k) {
             const uint32_t d = threadIdx.x + (uint32_t)k * kTileThreads;
-            if (d < D) gbase[d] = res[k];
+            if (d < D) gbase[d] = res[k] - excl[d];
         }
 #pragma unroll
         for (int j = 0; j < kTileItems; ++j) {
@@ -406,7 +407,7 @@ k_scatter(const uint64_t *__restrict__ keys, const V *__restrict__ vals, uint64_
             const uint64_t h = skey[i];
             const uint32_t g = group_of_h(h, range, gshift);
             const uint32_t d = SEG ? (g & (D - 1)) : (g >> dshift);
-            const uint32_t dst = gbase[d] + (i - excl[d]);
+            const uint32_t dst = gbase[d] + i;
             if (SLACK && dst >= ((uint64_t)seg * (SEG ? D : 0) + d + 1) * cap_out) {
                 atomicOr(err, kErrSortSlack);
                 continue;
@@ -840,8 +841,8 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
     }
     __syncthreads();
     block_scan(hist, excl, G, warp_sums);
-    for (uint32_t d = threadIdx.x; d < G; d += blockDim.x)
-        if (hist[d]) gbase[d] = atomicAdd(&cursor[D.group_base + d], hist[d]);
+    for (uint32_t d = threadIdx.x; d < G; d += blockDim.x)   // as in k_scatter: gbase[d] - excl[d]
+        if (hist[d]) gbase[d] = atomicAdd(&cursor[D.group_base + d], hist[d]) - excl[d];
 #pragma unroll
     for (int j = 0; j < kTileItems; ++j) {
         const uint32_t i = (uint32_t)j * kTileThreads + threadIdx.x;
@@ -854,7 +855,7 @@ k_scatter_batch(const uint64_t *__restrict__ keys, const V *__restrict__ vals, B
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
         const uint32_t d = group_of_h(skey[i], D.L.range, gshift);   // skey holds records h
-        const uint32_t dst = gbase[d] + (i - excl[d]);
+        const uint32_t dst = gbase[d] + i;
         keys_out[dst] = skey[i];
         vals_out[dst] = sval[i];
     }
