@@ -8,10 +8,13 @@
 //
 //   * groups of 64 buckets (about 8k keys) are the unit of the last pass;
 //   * one or two scatter passes bring the keys into group order.  Each pass
-//     works in tiles of 2048 keys: a shared-memory histogram and scan order
-//     the tile by digit in shared memory, one global atomic per (tile, digit)
-//     reserves the output range, and the tile is written out as contiguous
-//     runs per digit (coalesced stores, not scattered 8-byte writes);
+//     works in tiles of 4096 keys (2048 in the batched sort): a shared-memory
+//     histogram and scan order the tile by digit in shared memory, one global
+//     atomic per (tile, digit) reserves the output range, and the tile is
+//     written out as contiguous runs per digit (coalesced stores, not
+//     scattered 8-byte writes).  The output ranges come from counting passes
+//     over all keys, or, for layers sorted in two passes, from bins of fixed
+//     capacity (see the fixed-capacity section below);
 //   * the last pass sorts each group in shared memory (count, scan, place)
 //     and writes it out in order, together with the bucket offsets.
 //
