@@ -92,7 +92,7 @@ extern "C" {
 #define BURR_FLAG_TEST_WINDOW 2u  /* testing only: the band treats a pivot 136 or more slots past
                                      its bucket's first slot as leaving the on-chip window (the
                                      BURR_ERR_INTERNAL path of a real window overflow, which needs
-                                     a pivot 383 or more slots past its row's start) */
+                                     a pivot 382 or more slots past its row's start) */
 #define BURR_FLAG_TEST_SLACK 4u   /* testing only: a layer sorted in two scatter passes (more than
                                      2^16 buckets) sorts into bins of half their expected size, so
                                      that they overflow and the layer is sorted again exactly (the

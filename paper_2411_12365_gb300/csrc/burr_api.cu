@@ -665,7 +665,7 @@ int build_impl(const uint64_t *keys, const void *values, uint64_t n, uint32_t r,
             CK(cudaMemsetAsync(ctr, 0, 64, st), "clear counters");
         }
         const uint32_t e = (uint32_t)(hc[1] & 0xffffffffu);
-        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band window (510 slots)", l);
+        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band window (509 slots)", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
         S.nbumped = hc[0];
         if (onep) {
@@ -1133,7 +1133,7 @@ int build_batch_impl(const uint64_t *keys, const void *values, const std::vector
         CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st), "read error word");
         if (onep) CK(cudaMemcpyAsync(hdir.data(), tdir, hdir.size() * 4, cudaMemcpyDeviceToHost, st), "read ranks");
         CK(cudaStreamSynchronize(st), "layer");
-        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band window (510 slots)", l);
+        if (e & kErrRingOverflow) return fail(BURR_ERR_INTERNAL, "layer %u: pivot left the band window (509 slots)", l);
         if (e) return fail(BURR_ERR_INTERNAL, "layer %u: device error 0x%x", l, e);
         uint8_t *tbytes = nullptr;
         if (onep) {

@@ -95,8 +95,15 @@ struct Lookahead {
     static constexpr int value = kExact ? BURR_BAND_LOOKAHEAD_1PLUS : BURR_BAND_LOOKAHEAD_2BIT;
     static_assert(value >= 0 && value <= 8, "lookahead out of range");
 };
-constexpr int kLookMax = Lookahead<false>::value > Lookahead<true>::value ? Lookahead<false>::value
-                                                                          : Lookahead<true>::value;
+// Read-ahead of a 2-bit launch whose partitions are all resident at once (a
+// layer of few partitions): the SMs then have issue slots to spare, each warp's
+// chain of steps sets the time, and a third slot saves steps.  Measured with
+// every partition resident: layer-0 band of 10^8 keys 8.54 -> 8.35 ms, of 2^25
+// keys 6.96 -> 6.75 ms; when partitions outnumber the resident warps (10^9
+// keys) the extra registers cost a CTA per SM: 63.7 -> 71.4 ms.
+constexpr int kLookFew = 3;
+constexpr int kMaxOf(int a, int b) { return a > b ? a : b; }
+constexpr int kLookMax = kMaxOf(kMaxOf(Lookahead<false>::value, Lookahead<true>::value), kLookFew);
 
 // Tagged sets (1+-bit thresholds): the kTagRows lowest-offset rows of the set
 // carry one bit each in bits 33.. of the right-hand-side word, and a row's tag
@@ -438,7 +445,8 @@ __device__ int stream_insert(BandWarpSmem &S, uint32_t lo, uint32_t hi, uint32_t
 
 // Insert the rows of bucket [rs, re) whose offset lies in [olo, ohi) as one
 // set; on a dependency or overflow every row this call stored is removed.
-template <typename V, bool kExact>
+// kL: slots read ahead per step.
+template <typename V, bool kExact, int kL = Lookahead<kExact>::value>
 __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, uint32_t rs, uint32_t re,
                           uint32_t bB, uint32_t olo, uint32_t ohi, uint32_t &staged_base, int lane) {
     if (lane == 0) S.ncommit = 0;
@@ -449,7 +457,7 @@ __device__ int insert_set(BandWarpSmem &S, const BandArgs<V> &a, const Ctx &x, u
             stage_rows(S, a, x, base, cnt, bB, lane);
             staged_base = base;
         }
-        const int rc = stream_insert<Lookahead<kExact>::value>(S, S.first[olo], S.first[ohi], bB, window_of(x.L), lane);
+        const int rc = stream_insert<kL>(S, S.first[olo], S.first[ohi], bB, window_of(x.L), lane);
         if (rc != kOk) {
             rollback(S, S.ncommit, lane);
             if (rc == kOverflow && lane == 0) atomicOr(a.err, kErrRingOverflow);
@@ -590,8 +598,9 @@ __device__ __forceinline__ void flush(BandWarpSmem &S, const BandArgs<V> &a, con
 }
 
 // kExact: 1+-bit thresholds (exact per bucket) instead of 2-bit codes; a
-// template parameter so that each mode gets its own register allocation.
-template <typename V, bool kExact>
+// template parameter so that each mode gets its own register allocation.  kL:
+// slots read ahead per step (see kLookFew).
+template <typename V, bool kExact, int kL = Lookahead<kExact>::value>
 // All 1504 layer-0 partitions of 10^8 keys are resident at once when the
 // kernel takes at most 170 registers (six CTAs of two warps per SM).  Measured
 // with staging inline: at 186 registers (5 CTAs per SM) the layer-0 band took
@@ -681,12 +690,12 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                 texact = insert_tagged(S, a, x, rs, re, (uint32_t)bB, forced, staged, lane);
                 if (texact == L.B + 1u) return;   // ring overflow (recorded)
                 if (texact != kTagUnknown && texact > forced) {
-                    const int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, texact, L.B, staged, lane);
+                    const int rc = insert_set<V, kExact, kL>(S, a, x, rs, re, (uint32_t)bB, texact, L.B, staged, lane);
                     if (rc == kOverflow) return;
                     if (rc != kOk) texact = kTagUnknown;   // not expected: the rows at offsets >= t are independent
                 }
                 search = texact == kTagUnknown;
-            } else if (const int rc = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
+            } else if (const int rc = insert_set<V, kExact, kL>(S, a, x, rs, re, (uint32_t)bB, forced, L.B, staged, lane);
                        rc != kOk) {
                 if (rc == kOverflow) return;
                 if (L.fallback) {
@@ -704,7 +713,7 @@ __global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
                     code = 3;
                     for (int k = 1; k <= 2; ++k) {
                         if (lv[k] <= forced) continue;
-                        const int rc2 = insert_set<V, kExact>(S, a, x, rs, re, (uint32_t)bB, lv[k], L.B, staged, lane);
+                        const int rc2 = insert_set<V, kExact, kL>(S, a, x, rs, re, (uint32_t)bB, lv[k], L.B, staged, lane);
                         if (rc2 == kOverflow) return;
                         if (rc2 == kOk) {
                             code = (uint32_t)k;
@@ -938,6 +947,18 @@ cudaError_t band_impl(const LayerDesc &L, const uint64_t *keys, const V *vals, c
     if (L.mode == BURR_THRESH_1PLUS && !L.fallback) {
         if ((e = prefer_shared(k_band<V, true>)) != cudaSuccess) return e;
         k_band<V, true><<<grid, 32 * kBandWarps, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    // 2-bit: the deeper read-ahead where every CTA of the launch is resident at once
+    if ((e = prefer_shared(k_band<V, false, kLookFew>)) != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band<V, false, kLookFew>, 32 * kBandWarps, 0)) !=
+        cudaSuccess)
+        return e;
+    if ((uint64_t)grid <= (uint64_t)sms * (uint64_t)per_sm) {
+        k_band<V, false, kLookFew><<<grid, 32 * kBandWarps, 0, st>>>(a);
     } else {
         if ((e = prefer_shared(k_band<V, false>)) != cudaSuccess) return e;
         k_band<V, false><<<grid, 32 * kBandWarps, 0, st>>>(a);

@@ -37,7 +37,7 @@ ALPHA = 1.015
 P0, PL = 65536, 4096           # partition slots of layer 0 and of deeper layers
 THREADS = os.cpu_count() or 1
 N9 = 1_000_000_000
-WINDOW = 510                   # band kernel: 512-slot ring less its 2-slot read-ahead
+WINDOW = 509                   # band kernel: 512-slot ring less its deepest read-ahead (3 slots)
 B = 128
 
 
