@@ -92,11 +92,11 @@ def measured_peaks():
 
 
 def ncu_band_summary(kernel_src: str, path: str | None = None):
-    """DRAM bytes and warp instructions of one captured layer-0 band launch
-    (2-bit thresholds, 1-byte values) and its layer-0 key count, from the
+    """DRAM bytes and warp instructions of the captured layer-0 band launches
+    (2-bit thresholds, 1-byte values) and their layer-0 key count, from the
     committed ncu summary, if it was taken on the current kernel source; else
     None.  Both grow in proportion to the keys of the launch."""
-    path = path or os.path.join(ROOT, "profiles", "k_band_2e25_r8_traffic.txt")
+    path = path or os.path.join(ROOT, "profiles", "k_band_1e9_r8_traffic.txt")
     try:
         kv = {}
         for line in open(path):

@@ -13,7 +13,7 @@ BAND = os.path.join(ROOT, "paper_2411_12365_gb300", "csrc", "burr_band.cu")
 
 def test_committed_summary_matches_the_band_source():
     s = bench.ncu_band_summary(BAND)
-    assert s is not None, "profiles/k_band_2e25_r8_traffic.txt was taken on another band source"
+    assert s is not None, "profiles/k_band_1e9_r8_traffic.txt was taken on another band source"
     assert s["dram_bytes"] > 1e8 and s["warp_instructions"] > 1e9 and s["keys"] >= 1 << 20
 
 
