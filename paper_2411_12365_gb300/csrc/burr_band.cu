@@ -606,8 +606,13 @@ template <typename V, bool kExact, int kL = Lookahead<kExact>::value>
 // with staging inline: at 186 registers (5 CTAs per SM) the layer-0 band took
 // 15.5 ms instead of 9.7; with a 128-register cap (spills inside the
 // elimination loop) 13.4 ms.  With staging as a call it takes 128 without
-// such spills (see stage_rows).
-__global__ void __launch_bounds__(32 * kBandWarps) k_band(BandArgs<V> a) {
+// such spills (see stage_rows).  The 2-bit kernel for values wider than a
+// byte at two slots of read-ahead gets an explicit bound of 8 CTAs per SM:
+// without it ptxas gave it 139 registers (7 CTAs per SM; r = 16 at 10^9 keys:
+// layer-0 band 67.4 -> 72.7 ms); the other instantiations keep the bound on
+// threads alone (0 below), under which the one-byte kernel measured fastest.
+__global__ void __launch_bounds__(32 * kBandWarps, (sizeof(V) > 1 && !kExact && kL == 2) ? 8 : 0)
+    k_band(BandArgs<V> a) {
     __shared__ BandWarpSmem smem[kBandWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t gp = (uint64_t)blockIdx.x * kBandWarps + warp;
