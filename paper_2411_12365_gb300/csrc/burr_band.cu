@@ -13,9 +13,9 @@
 //     table does not depend on it either (unique solution with free slots 0).
 //   * So the warp first inserts the whole bucket as one set.  Most buckets
 //     insert without a dependency.  If the set is dependent it is rolled back
-//     and, with 2-bit thresholds, the bands [l2,l3), [l1,l2), [l0,l1) are
-//     inserted from the top until one is dependent, which fixes the threshold
-//     exactly as the row-by-row elimination in descending offset order would.
+//     and, with 2-bit thresholds, the rows [l1, B), then [l2, B), are tried as
+//     one set each until one inserts, which fixes the threshold exactly as the
+//     row-by-row elimination in descending offset order would.
 //   * With 1+-bit thresholds (exact threshold t in [0, B]) t is the least
 //     value for which the rows at offsets >= t insert.  The first pass over
 //     the bucket carries row tags and drops dependent rows instead of
