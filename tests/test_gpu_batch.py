@@ -90,6 +90,20 @@ def test_batch_base_case_heavy():
     _check_batch(sizes, rs, layers=1, partition_slots=1024, min_partition_slots=1024)
 
 
+@pytest.mark.parametrize("mode", [burr.THRESH_2BIT, burr.THRESH_1PLUS])
+def test_batch_with_split_band(mode):
+    """A batch layer of 4096 or more partitions bands in two launches (the
+    first 90% of the longest-first order, then the rest on a second stream),
+    the first launch's back-substitution beside the second, and each layer's
+    back-substitution runs beside the next layer over rotating band arrays:
+    every structure still equals its solo build."""
+    rng = np.random.default_rng(8)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(2000), np.log(60000), size=300))]
+    rs = [int(x) for x in rng.choice([1, 4, 8], size=len(sizes))]
+    assert sum(sizes) * 1.015 / 1024 > 4096 + 300          # partitions of layer 0
+    _check_batch(sizes, rs, partition_slots=1024, min_partition_slots=1024, threshold_mode=mode)
+
+
 def test_batch_rejects_too_large_structure():
     keys = I.keys_torch(9_000_000, "cuda")
     vals = I.values_torch(keys, 8)

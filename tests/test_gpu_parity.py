@@ -244,6 +244,16 @@ def test_host_inputs_streamed_into_the_sort():
     assert burr.build(hk.pin_memory(), vals, r).export() == want
 
 
+@pytest.mark.parametrize("mode", [burr.THRESH_2BIT, burr.THRESH_1PLUS])
+def test_split_band_matches_oracle(mode):
+    """A layer of 4096 or more partitions bands in two launches started
+    together (90% of the partitions, then the rest on a second stream), the
+    first launch's back-substitution beside the second; small launches read
+    three slots ahead, large ones two.  4.5*10^6 keys with 1024-slot
+    partitions give ~4,400 layer-0 partitions."""
+    _check_build(4_500_000, 8, seed=45, partition_slots=1024, min_partition_slots=1024, threshold_mode=mode)
+
+
 # Cut-point search (Sec. 3): cuts moved by the library's search kernel give
 # the same structure as the oracle's search
 
