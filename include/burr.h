@@ -489,6 +489,8 @@ int burr_server_handle(burr_server *s, uint64_t build_ticket, const burr_handle 
  * a query running on it is waited for. */
 int burr_server_release(burr_server *s, uint64_t build_ticket);
 
+/* A snapshot of the counters above, taken under the server's lock.
+ * BURR_ERR_INVALID if s or st is NULL. */
 int burr_server_stats(burr_server *s, burr_server_stats_t *st);
 
 /* Finish the running batch and queries, fail the builds still queued
