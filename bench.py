@@ -680,7 +680,7 @@ def run_plain(a, ws, rank, local, pg):
             out_len[0] = h.export(out=hx)
             h.free()
 
-        for _ in range(max(1, min(a.warmup, 2))):
+        for _ in range(max(1, min(a.warmup, 3))):
             e2e_step()
         torch.cuda.synchronize()
         barrier(pg)
