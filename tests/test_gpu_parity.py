@@ -301,6 +301,29 @@ def test_large_host_query_is_pipelined_and_exact(pinned):
 
 
 
+QUERY_STRIDE = 9728 * 256   # threads of the largest query grid: keys a thread's walk steps over
+
+
+@pytest.mark.parametrize("r", [1, 8, 16])
+def test_query_lengths_around_the_grid_stride(r):
+    """A query thread takes keys i, i + stride, ... and reads its next key
+    while the current one's table reads are in flight: lengths just below, at
+    and above one and two strides answer as the oracle does, key by key
+    (members and negatives interleaved)."""
+    keys, vals = _kv(1 << 20, r, seed=77)
+    h = burr.build(keys, vals, r)
+    ref = O.build(_u64(keys), _vals_np(vals), r=r)
+    assert ref.ok
+    neg = I.keys_torch(1 << 20, DEV, seed=77, offset=1 << 20)
+    pool = torch.stack([keys, neg], dim=1).reshape(-1)          # member, negative, member, ...
+    want_pool = np.stack([_vals_np(vals), ref.query(_u64(neg)).astype(np.uint32)], axis=1).reshape(-1)
+    for L in (QUERY_STRIDE - 1, QUERY_STRIDE, QUERY_STRIDE + 1, 2 * QUERY_STRIDE + 3):
+        idx = torch.arange(L, device=DEV) % pool.numel()
+        got = _vals_np(h.query(pool[idx]))
+        assert np.array_equal(got, want_pool[idx.cpu().numpy()]), L
+
+
+
 # Buckets of 64 start slots (the forced level after a cut is the whole bucket)
 
 @pytest.mark.parametrize("n,r,params", [
