@@ -8,8 +8,11 @@ library has not been built, every call raises: there is no fallback path.
 from __future__ import annotations
 
 import ctypes as C
+import operator
 import os
 import threading
+import weakref
+from collections.abc import Sequence
 
 import numpy as np
 
@@ -220,9 +223,12 @@ class Handle:
         self._h = ptr or None   # the library's handle pointer (an int), None once freed
         self.r = r
         self.owned = owned
+        self._batch = None      # the HandleBatch this handle belongs to (which then frees it)
+        self._idx = 0
 
     def __del__(self):
-        self.free()
+        if getattr(self, "_batch", None) is None:
+            self.free()
 
     def free(self):
         if not getattr(self, "owned", False):
@@ -230,6 +236,8 @@ class Handle:
         if getattr(self, "_h", None):
             load().burr_free(self._h)
             self._h = None
+            if self._batch is not None:
+                self._batch._ptrs[self._idx] = 0
 
     def query(self, keys, out=None, stream=None):
         """Values of `keys` (torch CUDA/CPU tensor or numpy array), same kind back."""
@@ -306,19 +314,77 @@ def import_export(buf: bytes, stream=None) -> Handle:
     return Handle(out.value, r)
 
 
-def free_all(handles) -> None:
-    """burr_free_many: release many handles (e.g. a batched build's) in one call."""
-    ptrs = [h._h for h in handles if getattr(h, "owned", False) and h._h]
-    if ptrs:
-        load().burr_free_many((C.c_void_p * len(ptrs))(*ptrs), len(ptrs))
-    for h in handles:
-        if getattr(h, "owned", False):
+class HandleBatch(Sequence):
+    """The structures of one batched build, in order.  Its handles are made on
+    first access (a batch of 10,000 structures does not build 10,000 Python
+    objects when only a few are used) and stay valid while they or the batch
+    are referenced; free_all(batch) releases every structure not yet freed in
+    one library call, and dropping the batch and its handles frees the rest."""
+
+    def __init__(self, ptrs, rs):
+        self._ptrs = ptrs                   # numpy uint64 handle pointers, 0 once freed
+        self._rs = rs
+        self._made = weakref.WeakValueDictionary()
+
+    def __len__(self):
+        return int(self._ptrs.size)
+
+    def _one(self, i):
+        h = self._made.get(i)
+        if h is None:
+            h = Handle(int(self._ptrs[i]), self._rs[i])
+            h._batch, h._idx = self, i
+            self._made[i] = h
+        return h
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self._one(j) for j in range(*i.indices(len(self)))]
+        n = len(self)
+        i = operator.index(i)
+        if i < 0:
+            i += n
+        if not 0 <= i < n:
+            raise IndexError(i)
+        return self._one(i)
+
+    def __iter__(self):
+        for i in range(len(self)):
+            yield self._one(i)
+
+    def free(self):
+        live = np.ascontiguousarray(self._ptrs[self._ptrs != 0])
+        if live.size:
+            load().burr_free_many(live.ctypes.data, int(live.size))
+        self._ptrs[:] = 0
+        for h in list(self._made.values()):
             h._h = None
 
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:   # interpreter shutdown: the library may be gone
+            pass
 
-def build_batch(keys, values, offsets, rs, params: Params | None = None, stream=None, **kw) -> list:
+
+def free_all(handles) -> None:
+    """burr_free_many: release many handles (e.g. a batched build's) in one call."""
+    if isinstance(handles, HandleBatch):
+        handles.free()
+        return
+    hs = [h for h in handles if getattr(h, "owned", False) and h._h]
+    if hs:
+        ptrs = [h._h for h in hs]
+        load().burr_free_many((C.c_void_p * len(ptrs))(*ptrs), len(ptrs))
+    for h in hs:
+        h._h = None
+        if h._batch is not None:
+            h._batch._ptrs[h._idx] = 0
+
+
+def build_batch(keys, values, offsets, rs, params: Params | None = None, stream=None, **kw) -> HandleBatch:
     """burr_build_batch: structure s owns keys[offsets[s]:offsets[s+1]] with r = rs[s].
-    Returns one Handle per structure."""
+    Returns the structures as a HandleBatch (a sequence of Handles, made on access)."""
     if params is None:
         params = default_params(**kw)
     offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64).astype(np.uint64))
@@ -332,8 +398,7 @@ def build_batch(keys, values, offsets, rs, params: Params | None = None, stream=
     outs = (C.c_void_p * S)()
     _check(load().burr_build_batch(kp, vp, offs, rr, S, C.byref(params), st, outs))
     # the pointers in one conversion (element-wise reads of a ctypes array cost ~1 us each)
-    ptrs = np.frombuffer(outs, dtype=np.uint64).tolist() if S else []
-    return [Handle(p, r) for p, r in zip(ptrs, rs_np.tolist())]
+    return HandleBatch(np.frombuffer(outs, dtype=np.uint64).copy(), rs_np.tolist())
 
 
 def stage_hash(keys, seed: int, layer_index: int, m: int, stream=None):
